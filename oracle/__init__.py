@@ -1,0 +1,208 @@
+"""Python access to the serial CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never loads it.  The arithmetic lives in ``rpq_oracle.c``: a
+plain, serial transcription of the paper's definitions (Section 3.1 and
+Eq. 1-3 for activation levels; Section 4, Algorithms 1-2 and Eq. 4-6 for the
+search).  This wrapper only marshals arrays.
+
+Parity is pinned for every function by the ``-m "not gpu"`` tests in
+``tests/test_oracle_*.py`` (Theorem 1 bounds, Theorem 5 against an independent
+bottleneck Dijkstra, a Bellman-Ford fixed point with the stop rules, brute
+force path enumeration on graphs of 20 nodes or fewer, Theorem 6 order
+independence, textbook BFS special case, hand-computed golden fixtures).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rpq_oracle.c")
+_LIB = os.path.join(_HERE, "_rpq_oracle.so")
+_lib = None
+INF = 255
+
+# field ids of orc_get (keep in step with the enum in rpq_oracle.c)
+(F_STATUS, F_NRES, F_RES_NODE, F_RES_SC, F_RES_SM, F_RES_SR, F_QPTR, F_QNODES, F_LAST_LEVEL,
+ F_LAST_EXPANDED, F_EACT, F_NEWHITS, F_CG_NODE, F_CG_SCORE, F_CG_LEVEL, F_NSEL, F_SEL, F_SEL_SC,
+ F_VC_ALL, F_VC_KW, F_EC, F_MATCHED, F_MATCH_LEVEL, F_SM, F_RAN) = range(25)
+
+
+def build_lib(force: bool = False) -> str:
+    """Compile the oracle (plain C, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build_lib())
+        P = ctypes.c_void_p
+        i32, i64, u64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        _lib.orc_activation.argtypes = [i32, i64, P, P, P, i32, f64, f64, P, P, P, P, P]
+        _lib.orc_activation.restype = ctypes.c_int
+        _lib.orc_search.argtypes = [i32, i64, P, P, P, i32, P, P, P, i32, P, i32, i32, i32, f64,
+                                    i32, i32, u64]
+        _lib.orc_search.restype = P
+        _lib.orc_get.argtypes = [P, i32, i32, i32, P]
+        _lib.orc_get.restype = i64
+        _lib.orc_get_h.argtypes = [P, i32, P, P, i32]
+        _lib.orc_get_h.restype = i32
+        _lib.orc_free.argtypes = [P]
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "arrays passed to the oracle must be C-contiguous"
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Activation:
+    a: np.ndarray      # uint8[m2] activation level per CSR entry
+    amax: np.ndarray   # uint8[n]
+    cnt: np.ndarray    # int64[m2] label count of Section 3.1
+    w: np.ndarray      # float64[m2] rescaled fine-grained weight
+    x: np.ndarray      # float64[m2] value before rounding (Eq. 3)
+
+
+def activation(row_ptr, col, label, n_labels, alpha, abar) -> Activation:
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    label = np.ascontiguousarray(label, np.uint16)
+    n = len(row_ptr) - 1
+    m2 = int(row_ptr[-1])
+    a = np.empty(m2, np.uint8)
+    amax = np.empty(n, np.uint8)
+    cnt = np.empty(m2, np.int64)
+    w = np.empty(m2, np.float64)
+    x = np.empty(m2, np.float64)
+    rc = _L().orc_activation(n, m2, _p(row_ptr), _p(col), _p(label), int(n_labels), float(alpha),
+                             float(abar), _p(a), _p(amax), _p(cnt), _p(w), _p(x))
+    if rc != 0:
+        raise ValueError("orc_activation rejected its arguments")
+    return Activation(a, amax, cnt, w, x)
+
+
+def dataset_activation(ds) -> Activation:
+    g = ds.graph
+    return activation(g.row_ptr, g.col, g.label, g.n_labels, ds.alpha, ds.abar)
+
+
+@dataclass
+class RunTrace:
+    h: np.ndarray          # uint8[n, nt]
+    stop: np.ndarray       # uint8[n] level at which the node stopped expanding (255 = never)
+    frontiers: list        # list of sorted int64 arrays, Q_l for l = 0..last_level
+    last_level: int
+    last_expanded: int
+    e_act: int
+    new_hits: int
+
+
+@dataclass
+class SearchResult:
+    status: int
+    nodes: np.ndarray      # int64[n_res] central node of each RPG, ranked
+    s_c: np.ndarray        # int32
+    s_m: np.ndarray        # int32
+    s_r: np.ndarray        # float64
+    central: RunTrace | None
+    marginal: RunTrace | None
+    cg_node: np.ndarray    # all identified CGs (identification order)
+    cg_score: np.ndarray
+    cg_level: np.ndarray
+    selected: np.ndarray   # top-w CG nodes, ordered by (S^c, id)
+    selected_sc: np.ndarray
+    vc_all: list           # V^c per selected CG
+    vc_kw: list            # V_C per selected CG
+    ec: list               # recovered CSR entries per selected CG
+    matched: np.ndarray
+    match_level: np.ndarray
+    sel_sm: np.ndarray
+
+
+def _get(L, h, field, r=0, g=0, dtype=np.int64):
+    cnt = L.orc_get(h, field, r, g, None)
+    out = np.empty(max(cnt, 0), dtype)
+    if cnt > 0:
+        L.orc_get(h, field, r, g, _p(out))
+    return out
+
+
+def _scalar(L, h, field, r=0, dtype=np.int32):
+    out = np.zeros(1, dtype)
+    L.orc_get(h, field, r, 0, _p(out))
+    return int(out[0])
+
+
+def _run(L, h, r, n) -> RunTrace | None:
+    if not _scalar(L, h, F_RAN, r):
+        return None
+    nt = L.orc_get_h(h, r, None, None, n)
+    H = np.empty((n, max(nt, 1)), np.uint8)
+    stop = np.empty(n, np.uint8)
+    L.orc_get_h(h, r, _p(H), _p(stop), n)
+    qptr = _get(L, h, F_QPTR, r)
+    qn = _get(L, h, F_QNODES, r)
+    fr = [qn[qptr[i]:qptr[i + 1]] for i in range(len(qptr) - 1)]
+    return RunTrace(h=H[:, :nt], stop=stop, frontiers=fr, last_level=_scalar(L, h, F_LAST_LEVEL, r),
+                    last_expanded=_scalar(L, h, F_LAST_EXPANDED, r),
+                    e_act=_scalar(L, h, F_EACT, r, np.int64), new_hits=_scalar(L, h, F_NEWHITS, r, np.int64))
+
+
+def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int, gamma: float = 0.5,
+           disable_stops: bool = False, exhaustive_marginal: bool = False, shuffle_seed: int = 0,
+           kw_ptr=None, kw_nodes=None) -> SearchResult:
+    """Run the oracle on one query.  ``ds_or_graph`` is an ``rpqgen.Dataset`` or
+    an ``rpqgen.Graph`` (then pass ``kw_ptr``/``kw_nodes``)."""
+    if hasattr(ds_or_graph, "graph"):
+        g = ds_or_graph.graph
+        kw_ptr, kw_nodes = ds_or_graph.kw_ptr, ds_or_graph.kw_nodes
+    else:
+        g = ds_or_graph
+    L = _L()
+    row_ptr = np.ascontiguousarray(g.row_ptr, np.int64)
+    col = np.ascontiguousarray(g.col, np.int32)
+    a = np.ascontiguousarray(a, np.uint8)
+    kw_ptr = np.ascontiguousarray(kw_ptr, np.int64)
+    kw_nodes = np.ascontiguousarray(kw_nodes, np.int32)
+    c = np.ascontiguousarray(central, np.int32)
+    m = np.ascontiguousarray(marginal, np.int32)
+    n = len(row_ptr) - 1
+    h = L.orc_search(n, int(row_ptr[-1]), _p(row_ptr), _p(col), _p(a), len(kw_ptr) - 1, _p(kw_ptr),
+                     _p(kw_nodes), _p(c), len(c), _p(m) if len(m) else None, len(m), int(k),
+                     int(max_depth), float(gamma), int(disable_stops), int(exhaustive_marginal),
+                     int(shuffle_seed))
+    try:
+        nsel = _scalar(L, h, F_NSEL)
+        res = SearchResult(
+            status=_scalar(L, h, F_STATUS),
+            nodes=_get(L, h, F_RES_NODE), s_c=_get(L, h, F_RES_SC, dtype=np.int32),
+            s_m=_get(L, h, F_RES_SM, dtype=np.int32), s_r=_get(L, h, F_RES_SR, dtype=np.float64),
+            central=_run(L, h, 0, n), marginal=_run(L, h, 1, n),
+            cg_node=_get(L, h, F_CG_NODE, 0), cg_score=_get(L, h, F_CG_SCORE, 0),
+            cg_level=_get(L, h, F_CG_LEVEL, 0),
+            selected=_get(L, h, F_SEL), selected_sc=_get(L, h, F_SEL_SC),
+            vc_all=[_get(L, h, F_VC_ALL, 0, g_) for g_ in range(nsel)],
+            vc_kw=[_get(L, h, F_VC_KW, 0, g_) for g_ in range(nsel)],
+            ec=[_get(L, h, F_EC, 0, g_) for g_ in range(nsel)],
+            matched=_get(L, h, F_MATCHED, dtype=np.int32),
+            match_level=_get(L, h, F_MATCH_LEVEL, dtype=np.int32),
+            sel_sm=_get(L, h, F_SM, dtype=np.int32))
+    finally:
+        L.orc_free(h)
+    return res
