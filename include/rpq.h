@@ -1,0 +1,227 @@
+/*
+ * rpq.h - C ABI of the B300 radial-pattern keyword search library (librpq.so).
+ *
+ * Radial-pattern keyword search (RAKS, arXiv 2001.06770): a query Q = {C, M}
+ * holds central keywords C (non-empty) and marginal keywords M (Definition 1).
+ * The library returns the top-k radial pattern graphs (Definition 6), each
+ * identified by its central node, with scores S^c (Eq. 4), S^m (Eq. 5) and
+ * S^r = gamma*S^c + (1-gamma)*S^m (Eq. 6).  All search work runs in CUDA
+ * kernels on one GPU; the knowledge graph stays resident in device memory.
+ *
+ * Conventions shared by every call:
+ *   - Return value: RPQ_OK (0) on success, a negative RPQ_E* code otherwise;
+ *     rpq_strerror() names the code and rpq_last_error() gives a message for
+ *     the calling thread's last failure.
+ *   - Host buffers are owned by the caller; the library never keeps a
+ *     pointer to them after the call returns.
+ *   - Device memory is allocated by the library (cudaMalloc) when a graph is
+ *     loaded and when a search slot is first used; rpq_free_kg releases it.
+ *   - Keyword ids index the postings given at load time; duplicate ids in a
+ *     query are allowed and behave as identical columns (a repeated marginal
+ *     keyword still counts towards |M|, which switches the PTC stop on).
+ *   - Calls on the same rpq_kg from several threads must be serialised by the
+ *     caller.
+ */
+#ifndef RPQ_H
+#define RPQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define RPQ_OK         0
+#define RPQ_EINVAL    (-1)  /* malformed graph or query, id out of range */
+#define RPQ_ENOMEM    (-2)  /* device or pinned host allocation failed */
+#define RPQ_ETIMEOUT  (-3)  /* a bounded device wait ran out */
+#define RPQ_ECUDA     (-4)  /* a CUDA runtime call failed */
+#define RPQ_ELIMIT    (-5)  /* input beyond a documented size limit */
+#define RPQ_EINTERNAL (-6)  /* a device-side consistency check failed */
+
+/* Documented limits of this build. */
+#define RPQ_MAX_NODES    (1 << 26)  /* node ids are packed in 26 bits */
+#define RPQ_MAX_LABELS   8192       /* edge labels must be < n_labels <= this */
+#define RPQ_MAX_LEVEL    63         /* activation levels and max_depth <= 63 */
+#define RPQ_MAX_KEYWORDS 8          /* per keyword set (central, marginal) */
+#define RPQ_MAX_K        64         /* top-k (and beam width w = k) */
+
+/* ------------------------------------------------------------------ graph */
+typedef struct rpq_kg rpq_kg; /* opaque, device resident */
+
+/* Knowledge graph handed to rpq_load_kg (Section 2: a bi-directed labelled
+ * graph - every original edge has its reverse - stored as CSR, Section 4.1).
+ *   n          number of nodes, 0 < n <= RPQ_MAX_NODES
+ *   m2         number of CSR entries (both directions), 0 <= m2 < 2^32
+ *   row_ptr    n+1 offsets, row_ptr[0] = 0, non-decreasing, row_ptr[n] = m2
+ *   col        m2 neighbour ids; each row strictly ascending, no self-loop
+ *   label      m2 edge labels < n_labels; the entry v->u carries the same
+ *              label as u->v (the reverse edge of Section 2)
+ *   n_labels   1 <= n_labels <= RPQ_MAX_LABELS
+ *   n_kw       number of keywords; kw_ptr has n_kw+1 offsets into kw_nodes
+ *   kw_nodes   node ids holding each keyword (V_t of Section 2), in [0, n)
+ *   alpha      scaling parameter of Eq. 1-2, 0 < alpha < 1 (paper: 0.5)
+ *   abar       average shortest hop count of the graph (Section 3.1), > 0
+ * Symmetry (each u->v has v->u with the same label) is checked on the device;
+ * a violation returns RPQ_EINVAL. */
+typedef struct {
+    int32_t n;
+    int64_t m2;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const uint16_t *label;
+    int32_t n_labels;
+    int32_t n_kw;
+    const int64_t *kw_ptr;
+    const int32_t *kw_nodes;
+    double alpha;
+    double abar;
+} rpq_kg_desc;
+
+/* Copy the graph to the current CUDA device and build the edge activation
+ * levels there (Section 3.1: label counts, w = log count, min-max rescale,
+ * Eq. 1-3 with round-half-up).  On success *out owns all device memory of the
+ * graph.  Errors: RPQ_EINVAL (malformed CSR, asymmetric edge or label,
+ * parameter out of range), RPQ_ELIMIT (a documented limit, or an activation
+ * level above RPQ_MAX_LEVEL), RPQ_ENOMEM, RPQ_ECUDA. */
+int rpq_load_kg(const rpq_kg_desc *desc, rpq_kg **out);
+
+/* Release every device and host resource of the graph.  NULL is accepted. */
+int rpq_free_kg(rpq_kg *kg);
+
+/* Export the device adjacency for inspection: adj[m2] receives each row's
+ * entries packed as (activation level << 26) | neighbour id, sorted ascending
+ * (that is by level, then by neighbour id); amax[n] receives each node's
+ * largest activation level (0 for an isolated node).  Either pointer may be
+ * NULL.  Host buffers, caller owned. */
+int rpq_kg_export(const rpq_kg *kg, uint32_t *adj, uint8_t *amax);
+
+/* Graph size and device bytes held by the graph and its search slots. */
+int rpq_kg_info(const rpq_kg *kg, int32_t *n, int64_t *m2, int64_t *device_bytes);
+
+/* ------------------------------------------------------------------ query */
+/* One radial pattern query (Definition 1; Table 2 parameters).
+ *   central, n_c   1 <= n_c <= RPQ_MAX_KEYWORDS keyword ids
+ *   marginal, n_m  0 <= n_m <= RPQ_MAX_KEYWORDS keyword ids (NULL if 0)
+ *   k              1 <= k <= RPQ_MAX_K; the CG beam width is w = k
+ *   max_depth      largest Glevel L, 0 <= L <= RPQ_MAX_LEVEL (paper: 20)
+ *   gamma          weight of Eq. 6, 0 <= gamma <= 1 (default 0.5) */
+typedef struct {
+    const int32_t *central;
+    int32_t n_c;
+    const int32_t *marginal;
+    int32_t n_m;
+    int32_t k;
+    int32_t max_depth;
+    double gamma;
+} rpq_query;
+
+/* One result: the central node of the RPG (or of the CG when M is empty) and
+ * its scores.  With M empty, s_m = 0 and s_r = s_c. */
+typedef struct {
+    int32_t node;
+    int32_t s_c;
+    int32_t s_m;
+    int32_t reserved;
+    double s_r;
+} rpq_result;
+
+/* Per-query work counters. */
+typedef struct {
+    int64_t e_act_central;  /* (column, edge) activations, central run */
+    int64_t e_act_marginal; /* same, marginal run */
+    int64_t hits_central;   /* first hits (h writes), central run */
+    int64_t hits_marginal;
+    int32_t levels_central; /* last identified Glevel of each run (-1: not run) */
+    int32_t levels_marginal;
+    int32_t n_cg;           /* CGs identified in the central run */
+    int32_t n_selected;     /* CGs kept (top-w) */
+} rpq_stats;
+
+/* Search one query (Sections 3-4): central run -> top-w CGs -> recovery of
+ * each CG's central keyword nodes (Algorithm 2) -> marginal run with the PTC
+ * stop -> RPG identification -> Eq. 6 scores -> top-k ordered by
+ * (S^r, node id).  out must hold q->k records; *n_out receives how many are
+ * valid (0 when no RPG exists, e.g. a keyword without keyword nodes).  stats
+ * may be NULL.  Host buffers; synchronous.  Errors: RPQ_EINVAL, RPQ_ELIMIT,
+ * RPQ_ENOMEM, RPQ_ECUDA, RPQ_EINTERNAL. */
+int rpq_search(rpq_kg *kg, const rpq_query *q, rpq_result *out, int32_t *n_out, rpq_stats *stats);
+
+/* Search nq independent queries.  out holds sum(k_i) records laid out in
+ * query order (query i starts at sum_{j<i} k_j); n_out[i] and status[i]
+ * receive each query's result count and return code; the call returns RPQ_OK
+ * when it ran (individual failures are reported in status) or an error for
+ * the whole batch.  Queries run concurrently on the device, each with its own
+ * search state; results equal those of rpq_search one query at a time.
+ * stats may be NULL or point to nq records. */
+int rpq_search_batch(rpq_kg *kg, const rpq_query *qs, int32_t nq, rpq_result *out, int32_t *n_out,
+                     int32_t *status, rpq_stats *stats);
+
+/* ---------------------------------------------------------------- tracing */
+/* Debug trace of one query, for comparison with a reference implementation.
+ * Every pointer may be NULL; sizes are in elements.
+ *   h_central    n * n_c bytes, row-major: h[v][j] = hit level of node v for
+ *                central keyword j, 255 when unreached (the Node-Keyword
+ *                Matrix of Section 4.2.1)
+ *   h_marginal   n * n_m bytes, same for the marginal run
+ *   frontier_*   concatenated frontiers Q_0, Q_1, ... of each run (each level
+ *                sorted ascending) with RPQ_MAX_LEVEL + 2 offsets in *_ptr;
+ *                *_levels receives the number of levels; at most *_cap
+ *                entries are written
+ *   cgs          all identified CGs as (node << 8 | score), ascending; up to
+ *                cg_cap entries; n_cgs receives the total
+ *   vc           V_C of each selected CG as (selected index << 26 | node),
+ *                ascending; up to vc_cap entries; n_vc receives the total
+ *   selected     top-w CG nodes ordered by (S^c, id); n_selected of them */
+typedef struct {
+    uint8_t *h_central;
+    uint8_t *h_marginal;
+    int64_t *frontier_c_ptr;
+    int32_t *frontier_c;
+    int64_t frontier_c_cap;
+    int32_t frontier_c_levels;
+    int64_t *frontier_m_ptr;
+    int32_t *frontier_m;
+    int64_t frontier_m_cap;
+    int32_t frontier_m_levels;
+    int64_t *cgs;
+    int64_t cg_cap;
+    int64_t n_cgs;
+    int64_t *vc;
+    int64_t vc_cap;
+    int64_t n_vc;
+    int32_t selected[RPQ_MAX_K];
+    int32_t n_selected;
+} rpq_trace_buf;
+
+/* Same search as rpq_search, also filling *trace (host buffers). */
+int rpq_trace(rpq_kg *kg, const rpq_query *q, rpq_result *out, int32_t *n_out, rpq_stats *stats,
+              rpq_trace_buf *trace);
+
+/* ------------------------------------------------- device-resident inputs */
+/* rpq_search_device: the same search with the keyword ids already in device
+ * memory and the results left in device memory, enqueued on the library's
+ * stream of search slot 0 without a host synchronisation.  d_keywords holds
+ * n_c central ids followed by n_m marginal ids (int32, device); d_out
+ * receives k rpq_result records and d_n_out one int32 (both device).  Keyword
+ * ids are checked on the device: an id outside [0, n_kw) sets the slot's
+ * error word, the query returns no result and rpq_sync_device reports
+ * RPQ_EINVAL.  The query shape (n_c, n_m, max_depth) selects a CUDA graph
+ * captured on first use and replayed for every later query of that shape. */
+int rpq_search_device(rpq_kg *kg, const int32_t *d_keywords, int32_t n_c, int32_t n_m, int32_t k,
+                      int32_t max_depth, double gamma, rpq_result *d_out, int32_t *d_n_out);
+
+/* Wait for searches issued with rpq_search_device and report the first
+ * device-side error since the previous call. */
+int rpq_sync_device(rpq_kg *kg);
+
+/* -------------------------------------------------------------- messages */
+const char *rpq_strerror(int code);
+const char *rpq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPQ_H */

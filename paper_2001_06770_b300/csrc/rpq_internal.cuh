@@ -1,0 +1,137 @@
+// Internal declarations of librpq (device structures, helpers).
+//
+// Device layout of a loaded graph (all in HBM, written once by rpq_load_kg):
+//   row_ptr  uint32[n+1]   CSR offsets (m2 < 2^32)
+//   adj      uint32[m2]    (a << 26) | neighbour, each row ascending, i.e.
+//                          sorted by activation level a, then neighbour id
+//   amax     uint8[n]      largest activation level of the row
+//   kw_ptr   uint32[n_kw+1], kw_nodes int32[]   keyword postings (V_t)
+//
+// Per-search state (one "slot"; several slots run concurrently):
+//   H        uint8[n][8]   Node-Keyword Matrix (Section 4.2.1), hit levels,
+//                          valid only where the visited bit is set
+//   vis      uint8[n]      visited bits, bit j = column j reached (read as
+//                          bytes, updated with 32-bit atomicOr)
+//   F[2]     uint32[n/32]  Frontier Flag Array, double buffered by level
+//   cf       uint32[n/32]  Joining Flag Array (node stopped expanding)
+//   stopl    uint8[n]      level at which the cf bit was set
+//   items    Item[n]       expansion work list of the current level
+//   cg       uint32[n]     identified CGs, (level << 26) | node
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rpq {
+
+constexpr uint32_t kNodeBits = 26;
+constexpr uint32_t kNodeMask = (1u << kNodeBits) - 1u;
+constexpr uint8_t kInf = 255;
+constexpr int kMaxCols = 8;
+constexpr int kMaxK = 64;
+constexpr int kMaxLevel = 63;
+constexpr int kMaxLabels = 8192;
+
+enum DevErr : uint32_t {
+  kErrNone = 0,
+  kErrBadCol = 1u << 0,    // neighbour id out of range or self-loop
+  kErrUnsorted = 1u << 1,  // row not strictly ascending
+  kErrBadLabel = 1u << 2,  // label >= n_labels
+  kErrAsym = 1u << 3,      // missing reverse entry or label differs
+  kErrLevel = 1u << 4,     // activation level above kMaxLevel
+  kErrKeyword = 1u << 5,   // keyword id out of range (device queries)
+  kErrOverflow = 1u << 6,  // a work list overflowed its capacity
+  kErrInternal = 1u << 7,
+};
+
+struct DevKG {
+  int32_t n;
+  uint32_t m2;
+  const uint32_t* row_ptr;
+  const uint32_t* adj;
+  const uint8_t* amax;
+  int32_t n_kw;
+  const uint32_t* kw_ptr;
+  const int32_t* kw_nodes;
+};
+
+// One expansion work item: a frontier node and its newly active segment.
+struct __align__(16) Item {
+  uint32_t node;
+  uint32_t seg_begin;  // first CSR entry of the segment
+  uint32_t off;        // exclusive prefix of segment lengths (work units)
+  uint8_t eq;          // columns with h == level
+  uint8_t lt;          // columns with h < level
+  uint16_t pad;
+};
+
+// Query parameters as the kernels read them (device copy in the slot).
+struct QueryDev {
+  int32_t kw[2 * kMaxCols];  // central ids then marginal ids
+  int32_t n_c, n_m, k, L;
+  double gamma;
+};
+
+// Control block of one slot, read and updated by the kernels of a search.
+struct Ctl {
+  unsigned long long work[2];  // per level parity: (items << 38) | work units
+  uint32_t done;               // current run finished
+  uint32_t level;              // last identified level of the current run
+  int32_t last_expanded;       // last level with an expansion (-1: none)
+  uint32_t nq;                 // |Q_l| of the current level
+  uint32_t ncg;                // CGs identified (central run)
+  uint32_t err;                // DevErr bits
+  uint32_t n_items, n_work;    // expansion list of the current level
+  uint32_t nsel;               // selected CGs
+  uint32_t nvc;                // (g, node) pairs of V_C
+  uint32_t rlist_n, ulist_n;   // recovery work lists
+  uint32_t n_res;
+  uint32_t topk_n[2];          // element counts of the top-k pass buffers
+  unsigned long long e_act[2];  // per run
+  unsigned long long hits[2];
+  int32_t levels[2];           // last identified level per run
+  int32_t sel[kMaxK];
+  uint8_t sel_sc[kMaxK];
+  uint8_t matched[kMaxK];
+  uint8_t sm[kMaxK];
+};
+
+struct DevSlot {
+  uint8_t* H;
+  uint32_t* vis;
+  uint32_t* F[2];
+  uint32_t* cf;
+  uint8_t* stopl;
+  Item* items;
+  uint32_t* cg;
+  uint32_t* topk[2];
+  unsigned long long* rmask;  // recovery: per-column CG mask per node
+  unsigned long long* vmask;  // recovery: union over columns
+  uint32_t* rlist;
+  uint32_t* ulist;
+  uint32_t* vcl;              // V_C pairs (g << 26 | node)
+  uint32_t cap;               // capacity (elements) of items/cg/lists
+  Ctl* ctl;
+  QueryDev* q;
+  void* res;                  // rpq_result[kMaxK] on the device
+  int32_t* n_res;
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint8_t vis_byte(const uint32_t* vis, uint32_t v) {
+  return reinterpret_cast<const uint8_t*>(vis)[v];
+}
+
+// First index in [lo, hi) of a sorted packed row whose level is >= x.
+__device__ __forceinline__ uint32_t seg_lower(const uint32_t* adj, uint32_t lo, uint32_t hi, uint32_t x) {
+  const uint32_t key = x << kNodeBits;
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(adj + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+int num_sms();
+
+}  // namespace rpq
