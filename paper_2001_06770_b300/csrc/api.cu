@@ -1,0 +1,541 @@
+// C ABI of librpq (include/rpq.h): validation, graph load, search slots,
+// CUDA graphs per query shape, batches over concurrent slots, tracing.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "rpq_host.h"
+
+namespace rpq {
+
+int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st);
+int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st);
+int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+void set_error(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = std::string(rpq_strerror(code)) + ": " + buf;
+}
+
+int dev_err_to_status(uint32_t err) {
+  if (!err) return RPQ_OK;
+  if (err & kErrKeyword) { set_error(RPQ_EINVAL, "keyword id out of range (device check)"); return RPQ_EINVAL; }
+  if (err & kErrOverflow) { set_error(RPQ_EINTERNAL, "a device work list overflowed"); return RPQ_EINTERNAL; }
+  set_error(RPQ_EINTERNAL, "device consistency check failed (flags 0x%x)", err);
+  return RPQ_EINTERNAL;
+}
+
+// One search slot: device state of one in-flight query, its stream, pinned
+// staging for results and the captured graphs of each query shape.
+struct Slot {
+  DevSlot d{};
+  cudaStream_t st = nullptr;
+  int64_t bytes = 0;
+  Ctl* h_ctl = nullptr;
+  rpq_result* h_res = nullptr;
+  std::vector<void*> allocs;
+  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  bool busy = false;
+  int32_t pending_k = 0;
+};
+
+static bool use_graphs() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_NO_GRAPH"); v = (e && *e && *e != '0') ? 0 : 1; }
+  return v == 1;
+}
+
+static void destroy_slot(Slot* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
+  if (s->h_res) cudaFreeHost(s->h_res);
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+static int create_slot(rpq_kg* kg, Slot** out) {
+  Slot* s = new Slot();
+  const size_t n = size_t(kg->dev.n);
+  const size_t nwords = (n + 31) / 32;
+  DevSlot& d = s->d;
+  d.cap = uint32_t(std::max<size_t>(n, 1));
+  auto A = [&](void** p, size_t bytes) -> int {
+    const int rc = alloc_device(p, bytes, &s->bytes);
+    if (rc == RPQ_OK) s->allocs.push_back(*p);
+    return rc;
+  };
+  int rc = RPQ_OK;
+#define SA(ptr, bytes) do { if (rc == RPQ_OK) rc = A((void**)&(ptr), (bytes)); } while (0)
+  SA(d.H, n * 8 + 16);
+  SA(d.vis, ((n + 3) / 4) * 4 + 16);
+  SA(d.F[0], nwords * 4 + 16);
+  SA(d.F[1], nwords * 4 + 16);
+  SA(d.cf, nwords * 4 + 16);
+  SA(d.stopl, n + 16);
+  SA(d.items, sizeof(Item) * d.cap);
+  SA(d.cg, sizeof(uint32_t) * d.cap);
+  const size_t tk = n / 32 + 4096;
+  SA(d.topk[0], sizeof(uint32_t) * tk);
+  SA(d.topk[1], sizeof(uint32_t) * tk);
+  SA(d.rmask, sizeof(unsigned long long) * d.cap);
+  SA(d.vmask, sizeof(unsigned long long) * d.cap);
+  SA(d.rlist, sizeof(uint32_t) * d.cap);
+  SA(d.ulist, sizeof(uint32_t) * d.cap);
+  SA(d.vcl, sizeof(uint32_t) * d.cap);
+  SA(d.sticky, 16);
+  SA(d.ctl, sizeof(Ctl));
+  SA(d.q, sizeof(QueryDev));
+  SA(d.res, sizeof(rpq_result) * kMaxK);
+  SA(d.n_res, 16);
+#undef SA
+  if (rc == RPQ_OK) {
+    // masks start at zero; the recovery kernel restores zero after each use
+    if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
+        cudaMemset(d.vmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
+        cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_res, sizeof(rpq_result) * kMaxK) != cudaSuccess) {
+      cudaGetLastError();
+      set_error(RPQ_ENOMEM, "search slot set-up failed");
+      rc = RPQ_ENOMEM;
+    }
+  }
+  if (rc != RPQ_OK) { destroy_slot(s); return rc; }
+  d.qlog = nullptr;
+  d.qcap = 0;
+  *out = s;
+  return RPQ_OK;
+}
+
+static int get_slot(rpq_kg* kg, size_t i, Slot** out) {
+  while (kg->slots.size() <= i) {
+    Slot* s = nullptr;
+    const int rc = create_slot(kg, &s);
+    if (rc != RPQ_OK) return rc;
+    kg->slots.push_back(s);
+    kg->device_bytes += s->bytes;
+  }
+  *out = kg->slots[i];
+  return RPQ_OK;
+}
+
+// Host validation of a query; fills qv.  Returns RPQ_OK, or an error, and
+// sets *empty when a keyword has no keyword node (no result is possible).
+static int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty) {
+  if (!q) { set_error(RPQ_EINVAL, "query is NULL"); return RPQ_EINVAL; }
+  if (q->n_c < 1 || q->n_c > kMaxCols || q->n_m < 0 || q->n_m > kMaxCols) {
+    set_error(RPQ_EINVAL, "need 1 <= n_c <= %d and 0 <= n_m <= %d (got %d, %d)", kMaxCols, kMaxCols, q->n_c, q->n_m);
+    return RPQ_EINVAL;
+  }
+  if (!q->central || (q->n_m > 0 && !q->marginal)) { set_error(RPQ_EINVAL, "keyword array is NULL"); return RPQ_EINVAL; }
+  if (q->k < 1 || q->k > kMaxK) { set_error(RPQ_EINVAL, "need 1 <= k <= %d (got %d)", kMaxK, q->k); return RPQ_EINVAL; }
+  if (q->max_depth < 0 || q->max_depth > kMaxLevel) {
+    set_error(RPQ_EINVAL, "need 0 <= max_depth <= %d (got %d)", kMaxLevel, q->max_depth);
+    return RPQ_EINVAL;
+  }
+  if (!(q->gamma >= 0.0 && q->gamma <= 1.0)) { set_error(RPQ_EINVAL, "need 0 <= gamma <= 1"); return RPQ_EINVAL; }
+  memset(qv, 0, sizeof(*qv));
+  *empty = false;
+  for (int i = 0; i < q->n_c + q->n_m; ++i) {
+    const int32_t kw = i < q->n_c ? q->central[i] : q->marginal[i - q->n_c];
+    if (kw < 0 || kw >= kg->dev.n_kw) {
+      set_error(RPQ_EINVAL, "keyword id %d out of range [0, %d)", kw, kg->dev.n_kw);
+      return RPQ_EINVAL;
+    }
+    if (kg->kw_ptr[kw + 1] == kg->kw_ptr[kw]) *empty = true;
+    qv->kw[i] = kw;
+  }
+  qv->n_c = q->n_c; qv->n_m = q->n_m; qv->k = q->k; qv->L = q->max_depth; qv->gamma = q->gamma;
+  return RPQ_OK;
+}
+
+static uint64_t shape_key(int n_c, int n_m, int L) { return (uint64_t(n_c) << 16) | (uint64_t(n_m) << 8) | uint64_t(L); }
+
+// Enqueue the body of a query: replay (or capture, then replay) the graph of
+// its shape, or launch the kernels directly.
+static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
+  if (!use_graphs()) {
+    RPQ_CUDA(cudaGetLastError());
+    return launch_query_body(kg->dev, s->d, n_m, L, s->st);
+  }
+  const uint64_t key = shape_key(n_c, n_m, L);
+  auto it = s->graphs.find(key);
+  if (it == s->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st);
+    const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    if (rc != RPQ_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      set_error(RPQ_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+      return RPQ_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { set_error(RPQ_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie)); return RPQ_ECUDA; }
+    it = s->graphs.emplace(key, exec).first;
+  }
+  RPQ_CUDA(cudaGraphLaunch(it->second, s->st));
+  return RPQ_OK;
+}
+
+// Start a validated query on a slot (asynchronous).
+static int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
+  int rc = launch_query_setup(s->d, qv, nullptr, s->st);
+  if (rc != RPQ_OK) { set_error(RPQ_ECUDA, "launch failed: %s", cudaGetErrorString(cudaGetLastError())); return rc; }
+  rc = enqueue_body(kg, s, qv.n_c, qv.n_m, qv.L);
+  if (rc != RPQ_OK) return rc;
+  RPQ_CUDA(cudaMemcpyAsync(s->h_ctl, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->st));
+  RPQ_CUDA(cudaMemcpyAsync(s->h_res, s->d.res, sizeof(rpq_result) * size_t(qv.k), cudaMemcpyDeviceToHost, s->st));
+  s->busy = true;
+  s->pending_k = qv.k;
+  return RPQ_OK;
+}
+
+static void fill_stats(const Ctl& c, rpq_stats* st) {
+  if (!st) return;
+  st->e_act_central = int64_t(c.e_act[0]);
+  st->e_act_marginal = int64_t(c.e_act[1]);
+  st->hits_central = int64_t(c.hits[0]);
+  st->hits_marginal = int64_t(c.hits[1]);
+  st->levels_central = c.levels[0];
+  st->levels_marginal = c.levels[1];
+  st->n_cg = int32_t(c.ncg);
+  st->n_selected = int32_t(c.nsel);
+}
+
+// Wait for the slot's query and copy its results out.
+static int finish_query(Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
+  s->busy = false;
+  RPQ_CUDA(cudaStreamSynchronize(s->st));
+  const Ctl& c = *s->h_ctl;
+  const int rc = dev_err_to_status(c.err);
+  if (rc != RPQ_OK) return rc;
+  const int32_t nr = int32_t(std::min<uint32_t>(c.n_res, uint32_t(s->pending_k)));
+  if (out && nr) memcpy(out, s->h_res, sizeof(rpq_result) * size_t(nr));
+  if (n_out) *n_out = nr;
+  fill_stats(c, stats);
+  return RPQ_OK;
+}
+
+static void empty_result(int32_t* n_out, rpq_stats* stats) {
+  if (n_out) *n_out = 0;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->levels_central = stats->levels_marginal = -1;
+  }
+}
+
+static int slot_count() {
+  static int v = 0;
+  if (!v) {
+    const char* e = getenv("RPQ_SLOTS");
+    v = (e && atoi(e) > 0) ? std::min(atoi(e), 256) : 8;
+  }
+  return v;
+}
+
+}  // namespace rpq
+
+using namespace rpq;
+
+extern "C" {
+
+const char* rpq_strerror(int code) {
+  switch (code) {
+    case RPQ_OK: return "RPQ_OK";
+    case RPQ_EINVAL: return "RPQ_EINVAL";
+    case RPQ_ENOMEM: return "RPQ_ENOMEM";
+    case RPQ_ETIMEOUT: return "RPQ_ETIMEOUT";
+    case RPQ_ECUDA: return "RPQ_ECUDA";
+    case RPQ_ELIMIT: return "RPQ_ELIMIT";
+    case RPQ_EINTERNAL: return "RPQ_EINTERNAL";
+  }
+  return "RPQ_E(unknown)";
+}
+
+const char* rpq_last_error(void) { return g_last_error.c_str(); }
+
+int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
+  if (!d || !out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  *out = nullptr;
+  if (d->n <= 0 || d->n > RPQ_MAX_NODES) { set_error(RPQ_ELIMIT, "n = %d outside (0, %d]", d->n, RPQ_MAX_NODES); return d->n <= 0 ? RPQ_EINVAL : RPQ_ELIMIT; }
+  if (d->m2 < 0 || d->m2 >= (int64_t(1) << 32)) { set_error(RPQ_ELIMIT, "m2 = %lld outside [0, 2^32)", (long long)d->m2); return RPQ_ELIMIT; }
+  if (!d->row_ptr || (d->m2 > 0 && (!d->col || !d->label)) || !d->kw_ptr || d->n_kw < 0) {
+    set_error(RPQ_EINVAL, "missing graph array"); return RPQ_EINVAL;
+  }
+  if (d->n_labels < 1 || d->n_labels > RPQ_MAX_LABELS) { set_error(RPQ_ELIMIT, "n_labels = %d outside [1, %d]", d->n_labels, RPQ_MAX_LABELS); return RPQ_ELIMIT; }
+  if (!(d->alpha > 0.0 && d->alpha < 1.0)) { set_error(RPQ_EINVAL, "alpha must lie in (0, 1)"); return RPQ_EINVAL; }
+  if (!(d->abar > 0.0) || !(d->abar < 1e6)) { set_error(RPQ_EINVAL, "abar must be positive"); return RPQ_EINVAL; }
+  if (d->row_ptr[0] != 0 || d->row_ptr[d->n] != d->m2) { set_error(RPQ_EINVAL, "row_ptr must start at 0 and end at m2"); return RPQ_EINVAL; }
+  for (int64_t i = 0; i < d->n; ++i)
+    if (d->row_ptr[i + 1] < d->row_ptr[i]) { set_error(RPQ_EINVAL, "row_ptr decreases at %lld", (long long)i); return RPQ_EINVAL; }
+  if (d->kw_ptr[0] != 0) { set_error(RPQ_EINVAL, "kw_ptr[0] must be 0"); return RPQ_EINVAL; }
+  for (int64_t i = 0; i < d->n_kw; ++i)
+    if (d->kw_ptr[i + 1] < d->kw_ptr[i]) { set_error(RPQ_EINVAL, "kw_ptr decreases at %lld", (long long)i); return RPQ_EINVAL; }
+  const int64_t npost = d->kw_ptr[d->n_kw];
+  if (npost >= (int64_t(1) << 32)) { set_error(RPQ_ELIMIT, "too many postings"); return RPQ_ELIMIT; }
+  if (npost > 0 && !d->kw_nodes) { set_error(RPQ_EINVAL, "kw_nodes is NULL"); return RPQ_EINVAL; }
+  for (int64_t i = 0; i < npost; ++i)
+    if (d->kw_nodes[i] < 0 || d->kw_nodes[i] >= d->n) { set_error(RPQ_EINVAL, "kw_nodes[%lld] out of range", (long long)i); return RPQ_EINVAL; }
+
+  rpq_kg* kg = new rpq_kg();
+  cudaGetDevice(&kg->device);
+  kg->m2 = d->m2;
+  kg->alpha = d->alpha;
+  kg->abar = d->abar;
+  kg->kw_ptr.assign(d->kw_ptr, d->kw_ptr + d->n_kw + 1);
+  int rc = build_graph(kg, d);
+  if (rc == RPQ_OK) {
+    std::vector<uint32_t> kp(size_t(d->n_kw) + 1);
+    for (int64_t i = 0; i <= d->n_kw; ++i) kp[i] = uint32_t(d->kw_ptr[i]);
+    rc = alloc_device((void**)&kg->d_kw_ptr, sizeof(uint32_t) * kp.size(), &kg->device_bytes);
+    if (rc == RPQ_OK) rc = alloc_device((void**)&kg->d_kw_nodes, sizeof(int32_t) * size_t(std::max<int64_t>(npost, 1)), &kg->device_bytes);
+    if (rc == RPQ_OK && (cudaMemcpy(kg->d_kw_ptr, kp.data(), sizeof(uint32_t) * kp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                         (npost > 0 && cudaMemcpy(kg->d_kw_nodes, d->kw_nodes, sizeof(int32_t) * size_t(npost), cudaMemcpyHostToDevice) != cudaSuccess))) {
+      set_error(RPQ_ECUDA, "postings upload failed");
+      rc = RPQ_ECUDA;
+    }
+  }
+  if (rc != RPQ_OK) { rpq_free_kg(kg); return rc; }
+  kg->dev.n = d->n;
+  kg->dev.m2 = uint32_t(d->m2);
+  kg->dev.row_ptr = kg->d_row_ptr;
+  kg->dev.adj = kg->d_adj;
+  kg->dev.amax = kg->d_amax;
+  kg->dev.n_kw = d->n_kw;
+  kg->dev.kw_ptr = kg->d_kw_ptr;
+  kg->dev.kw_nodes = kg->d_kw_nodes;
+  *out = kg;
+  return RPQ_OK;
+}
+
+int rpq_free_kg(rpq_kg* kg) {
+  if (!kg) return RPQ_OK;
+  for (Slot* s : kg->slots) destroy_slot(s);
+  cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax);
+  cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);
+  delete kg;
+  return RPQ_OK;
+}
+
+int rpq_kg_export(const rpq_kg* kg, uint32_t* adj, uint8_t* amax) {
+  if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
+  if (adj && kg->m2) RPQ_CUDA(cudaMemcpy(adj, kg->d_adj, sizeof(uint32_t) * size_t(kg->m2), cudaMemcpyDeviceToHost));
+  if (amax) RPQ_CUDA(cudaMemcpy(amax, kg->d_amax, size_t(kg->dev.n), cudaMemcpyDeviceToHost));
+  return RPQ_OK;
+}
+
+int rpq_kg_info(const rpq_kg* kg, int32_t* n, int64_t* m2, int64_t* device_bytes) {
+  if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
+  if (n) *n = kg->dev.n;
+  if (m2) *m2 = kg->m2;
+  if (device_bytes) *device_bytes = kg->device_bytes;
+  return RPQ_OK;
+}
+
+int rpq_search(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
+  if (!kg || !out || !n_out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  QueryDev qv;
+  bool empty = false;
+  int rc = check_query(kg, q, &qv, &empty);
+  if (rc != RPQ_OK) return rc;
+  if (empty) { empty_result(n_out, stats); return RPQ_OK; }
+  Slot* s = nullptr;
+  rc = get_slot(kg, 0, &s);
+  if (rc != RPQ_OK) return rc;
+  rc = start_query(kg, s, qv);
+  if (rc != RPQ_OK) { s->busy = false; cudaStreamSynchronize(s->st); return rc; }
+  return finish_query(s, out, n_out, stats);
+}
+
+int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* out, int32_t* n_out,
+                     int32_t* status, rpq_stats* stats) {
+  if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
+  const int nslots = std::max(1, std::min<int>(slot_count(), nq));
+  std::vector<Slot*> slots(size_t(nslots), nullptr);
+  for (int i = 0; i < nslots; ++i) {
+    const int rc = get_slot(kg, size_t(i), &slots[size_t(i)]);
+    if (rc != RPQ_OK) return rc;
+  }
+  std::vector<int64_t> base(size_t(nq) + 1, 0);
+  for (int32_t i = 0; i < nq; ++i) base[size_t(i) + 1] = base[size_t(i)] + std::max(qs[i].k, 0);
+  std::vector<int32_t> owner(size_t(nslots), -1);   // query running on each slot
+  auto collect = [&](int si) {
+    const int32_t qi = owner[size_t(si)];
+    if (qi < 0) return;
+    status[qi] = finish_query(slots[size_t(si)], out + base[size_t(qi)], &n_out[qi], stats ? &stats[qi] : nullptr);
+    if (status[qi] != RPQ_OK) n_out[qi] = 0;
+    owner[size_t(si)] = -1;
+  };
+  for (int32_t i = 0; i < nq; ++i) {
+    QueryDev qv;
+    bool empty = false;
+    n_out[i] = 0;
+    status[i] = check_query(kg, &qs[i], &qv, &empty);
+    if (status[i] != RPQ_OK) continue;
+    if (empty) { empty_result(&n_out[i], stats ? &stats[i] : nullptr); continue; }
+    const int si = int(i % nslots);
+    collect(si);
+    status[i] = start_query(kg, slots[size_t(si)], qv);
+    if (status[i] == RPQ_OK) owner[size_t(si)] = i;
+  }
+  for (int si = 0; si < nslots; ++si) collect(si);
+  return RPQ_OK;
+}
+
+int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, rpq_stats* stats, rpq_trace_buf* tr) {
+  if (!kg || !out || !n_out || !tr) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  QueryDev qv;
+  bool empty = false;
+  int rc = check_query(kg, q, &qv, &empty);
+  if (rc != RPQ_OK) return rc;
+  tr->n_cgs = 0; tr->n_vc = 0; tr->n_selected = 0; tr->frontier_c_levels = 0; tr->frontier_m_levels = 0;
+  if (empty) { empty_result(n_out, stats); return RPQ_OK; }
+  Slot* s = nullptr;
+  rc = get_slot(kg, 0, &s);
+  if (rc != RPQ_OK) return rc;
+  const size_t n = size_t(kg->dev.n);
+  const size_t qcap = std::min<size_t>(n * size_t(qv.L + 1), size_t(1) << 28);
+  uint32_t* d_qlog = nullptr;
+  rc = alloc_device((void**)&d_qlog, sizeof(uint32_t) * qcap, nullptr);
+  if (rc != RPQ_OK) return rc;
+  DevSlot d = s->d;
+  d.qlog = d_qlog;
+  d.qcap = uint32_t(qcap);
+  std::vector<uint8_t> H(n * 8), vis(((n + 3) / 4) * 4);
+  std::vector<uint32_t> qlog;
+  Ctl c{};
+  auto frontiers = [&](uint32_t from, uint32_t to, int64_t* ptr, int32_t* dst, int64_t cap, int32_t* levels) {
+    std::vector<uint32_t> e(qlog.begin() + from, qlog.begin() + to);
+    std::sort(e.begin(), e.end());   // by level, then node
+    int maxl = -1;
+    for (uint32_t x : e) maxl = std::max<int>(maxl, int(x >> kNodeBits));
+    *levels = maxl + 1;
+    if (ptr) {
+      size_t p = 0;
+      for (int l = 0; l <= kMaxLevel + 1; ++l) {
+        ptr[l] = int64_t(p);
+        while (p < e.size() && int(e[p] >> kNodeBits) == l) {
+          if (dst && int64_t(p) < cap) dst[p] = int32_t(e[p] & kNodeMask);
+          ++p;
+        }
+      }
+    }
+  };
+  auto hmat = [&](uint8_t* dst, int nt) {
+    if (!dst) return;
+    for (size_t v = 0; v < n; ++v)
+      for (int j = 0; j < nt; ++j) dst[v * size_t(nt) + size_t(j)] = ((vis[v] >> j) & 1) ? H[v * 8 + size_t(j)] : kInf;
+  };
+  auto fail = [&](int code) { cudaFree(d_qlog); return code; };
+#define TC(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error(RPQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return fail(RPQ_ECUDA); } } while (0)
+  if (launch_query_setup(d, qv, nullptr, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
+  if (launch_central_part(kg->dev, d, qv.L, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
+  TC(cudaStreamSynchronize(s->st));
+  TC(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  TC(cudaMemcpy(H.data(), d.H, n * 8, cudaMemcpyDeviceToHost));
+  TC(cudaMemcpy(vis.data(), d.vis, n, cudaMemcpyDeviceToHost));
+  const uint32_t nqc = std::min<uint32_t>(c.qlog_n, uint32_t(qcap));
+  qlog.resize(nqc);
+  if (nqc) TC(cudaMemcpy(qlog.data(), d_qlog, sizeof(uint32_t) * nqc, cudaMemcpyDeviceToHost));
+  hmat(tr->h_central, qv.n_c);
+  frontiers(0, nqc, tr->frontier_c_ptr, tr->frontier_c, tr->frontier_c_cap, &tr->frontier_c_levels);
+  {
+    std::vector<uint32_t> cg(c.ncg);
+    if (c.ncg) TC(cudaMemcpy(cg.data(), d.cg, sizeof(uint32_t) * c.ncg, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> cgs;
+    for (uint32_t x : cg) cgs.push_back((int64_t(x & kNodeMask) << 8) | int64_t(x >> kNodeBits));
+    std::sort(cgs.begin(), cgs.end());
+    tr->n_cgs = int64_t(cgs.size());
+    if (tr->cgs) for (size_t i = 0; i < cgs.size() && int64_t(i) < tr->cg_cap; ++i) tr->cgs[i] = cgs[i];
+    tr->n_selected = int32_t(c.nsel);
+    for (uint32_t i = 0; i < c.nsel; ++i) tr->selected[i] = c.sel[i];
+  }
+  if (launch_marginal_part(kg->dev, d, qv.n_m, qv.L, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
+  TC(cudaStreamSynchronize(s->st));
+  TC(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  {
+    std::vector<uint32_t> vcl(std::min<uint32_t>(c.nvc, d.cap));
+    if (!vcl.empty()) TC(cudaMemcpy(vcl.data(), d.vcl, sizeof(uint32_t) * vcl.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> vc(vcl.begin(), vcl.end());
+    std::sort(vc.begin(), vc.end());
+    tr->n_vc = int64_t(vc.size());
+    if (tr->vc) for (size_t i = 0; i < vc.size() && int64_t(i) < tr->vc_cap; ++i) tr->vc[i] = vc[i];
+  }
+  if (qv.n_m > 0 && c.levels[1] >= 0) {
+    TC(cudaMemcpy(H.data(), d.H, n * 8, cudaMemcpyDeviceToHost));
+    TC(cudaMemcpy(vis.data(), d.vis, n, cudaMemcpyDeviceToHost));
+    hmat(tr->h_marginal, qv.n_m);
+    const uint32_t nqa = std::min<uint32_t>(c.qlog_n, uint32_t(qcap));
+    qlog.resize(nqa);
+    if (nqa > nqc) TC(cudaMemcpy(qlog.data() + nqc, d_qlog + nqc, sizeof(uint32_t) * (nqa - nqc), cudaMemcpyDeviceToHost));
+    frontiers(nqc, nqa, tr->frontier_m_ptr, tr->frontier_m, tr->frontier_m_cap, &tr->frontier_m_levels);
+  }
+  rpq_result res[kMaxK];
+  TC(cudaMemcpy(res, d.res, sizeof(rpq_result) * size_t(qv.k), cudaMemcpyDeviceToHost));
+#undef TC
+  cudaFree(d_qlog);
+  rc = dev_err_to_status(c.err);
+  if (c.qlog_n > qcap) { set_error(RPQ_ELIMIT, "trace frontier log overflow"); rc = RPQ_ELIMIT; }
+  if (rc != RPQ_OK) return rc;
+  const int32_t nr = int32_t(std::min<uint32_t>(c.n_res, uint32_t(qv.k)));
+  memcpy(out, res, sizeof(rpq_result) * size_t(nr));
+  *n_out = nr;
+  fill_stats(c, stats);
+  return RPQ_OK;
+}
+
+int rpq_search_device(rpq_kg* kg, const int32_t* d_keywords, int32_t n_c, int32_t n_m, int32_t k, int32_t max_depth,
+                      double gamma, rpq_result* d_out, int32_t* d_n_out) {
+  if (!kg || !d_keywords || !d_out || !d_n_out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  if (n_c < 1 || n_c > kMaxCols || n_m < 0 || n_m > kMaxCols || k < 1 || k > kMaxK || max_depth < 0 ||
+      max_depth > kMaxLevel || !(gamma >= 0.0 && gamma <= 1.0)) {
+    set_error(RPQ_EINVAL, "query parameter out of range");
+    return RPQ_EINVAL;
+  }
+  Slot* s = nullptr;
+  int rc = get_slot(kg, 0, &s);
+  if (rc != RPQ_OK) return rc;
+  QueryDev qv;
+  memset(&qv, 0, sizeof(qv));
+  qv.n_c = n_c; qv.n_m = n_m; qv.k = k; qv.L = max_depth; qv.gamma = gamma;
+  rc = launch_query_setup(s->d, qv, d_keywords, s->st);
+  if (rc != RPQ_OK) { set_error(RPQ_ECUDA, "launch failed"); return rc; }
+  rc = enqueue_body(kg, s, n_c, n_m, max_depth);
+  if (rc != RPQ_OK) return rc;
+  RPQ_CUDA(cudaMemcpyAsync(d_out, s->d.res, sizeof(rpq_result) * size_t(k), cudaMemcpyDeviceToDevice, s->st));
+  RPQ_CUDA(cudaMemcpyAsync(d_n_out, s->d.n_res, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->st));
+  return RPQ_OK;
+}
+
+int rpq_sync_device(rpq_kg* kg) {
+  if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
+  if (kg->slots.empty()) return RPQ_OK;
+  Slot* s = kg->slots[0];
+  RPQ_CUDA(cudaStreamSynchronize(s->st));
+  uint32_t err = 0;
+  RPQ_CUDA(cudaMemcpy(&err, s->d.sticky, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (err) RPQ_CUDA(cudaMemset(s->d.sticky, 0, sizeof(uint32_t)));
+  return dev_err_to_status(err);
+}
+
+}  // extern "C"

@@ -77,7 +77,9 @@ struct Ctl {
   uint32_t done;               // current run finished
   uint32_t level;              // last identified level of the current run
   int32_t last_expanded;       // last level with an expansion (-1: none)
-  uint32_t nq;                 // |Q_l| of the current level
+  uint32_t nq[2];              // |Q_l| per level parity
+  uint32_t n_matched;          // selected CGs matched so far (marginal run)
+  uint32_t qlog_n;             // entries of the frontier log (trace mode)
   uint32_t ncg;                // CGs identified (central run)
   uint32_t err;                // DevErr bits
   uint32_t n_items, n_work;    // expansion list of the current level
@@ -110,6 +112,9 @@ struct DevSlot {
   uint32_t* ulist;
   uint32_t* vcl;              // V_C pairs (g << 26 | node)
   uint32_t cap;               // capacity (elements) of items/cg/lists
+  uint32_t* qlog;             // trace mode: (level << 26 | node) of every Q_l entry
+  uint32_t qcap;
+  uint32_t* sticky;           // device error bits kept across queries
   Ctl* ctl;
   QueryDev* q;
   void* res;                  // rpq_result[kMaxK] on the device

@@ -1,0 +1,664 @@
+// Search kernels of one radial-pattern query (Section 4).
+//
+// One query runs as a fixed sequence of launches on the slot's stream:
+//   k_set_query                       copy parameters, reset the control block
+//   per run (central, then marginal):
+//     memsets of vis / F / cf, k_seed (Section 4.2.1 initialisation)
+//     for l = 0..L:  k_enqueue(l)     frontier enqueue + reset (4.2.2) and
+//                                     result identification (4.2.3,
+//                                     Theorem 3; PTC stop; RPG match)
+//                    k_expand(l)      termination decision + expansion
+//                                     (Algorithm 1) of the newly active edges
+//   after the central run: k_topk_pass x4, k_select (top-w CGs),
+//                          k_recover (Algorithm 2 -> V_C of each CG)
+//   at the end:            k_results (Eq. 6, top-k by (S^r, id))
+// Every kernel first reads the control block and returns at once when the
+// current run has already finished, so the sequence can be captured once per
+// query shape (|C|, |M|, L) as a CUDA graph and replayed.
+//
+// Exactness: the expansion at level l touches, for frontier node v and
+// column j, only the edges with max(h[v][j], a) == l (the rows are sorted by
+// a, so they form one segment).  An edge with a smaller max was already
+// handled at that earlier level by the same node (which was in the frontier
+// then, because it is retained while it has an edge with a > level), so
+// skipping Algorithm 1's re-scan changes no h value.  Writes of h store the
+// same value l+1 whoever wins (Theorem 6); the atomicOr on the visited byte
+// only decides which thread performs the single write.
+#include <algorithm>
+#include <cstdio>
+
+#include "rpq_host.h"
+
+namespace rpq {
+
+namespace {
+
+constexpr int kEnqThreads = 256;
+constexpr int kEnqRounds = 4;
+constexpr int kExpThreads = 256;
+constexpr int kExpUnits = 4;                       // work units per thread per tile
+constexpr int kExpTile = kExpThreads * kExpUnits;  // 1024
+constexpr int kRecThreads = 1024;
+constexpr int kTopkThreads = 1024;
+constexpr int kTopkChunk = 4096;
+constexpr unsigned long long kWorkBits = 38;
+constexpr unsigned long long kWorkMask = (1ull << kWorkBits) - 1ull;
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {
+  const uint32_t lane = lane_id();
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= uint32_t(o)) v += t;
+  }
+  return v;
+}
+
+// Exclusive block scan of one 64-bit value per thread; *total gets the sum.
+// s_warp must hold 33 entries.  Contains __syncthreads.
+__device__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_warp, uint64_t* total) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t incl = warp_incl_scan(v);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t t = lane < nw ? s_warp[lane] : 0;
+    const uint64_t ti = warp_incl_scan(t);
+    if (lane < nw) s_warp[lane] = ti - t;
+    if (lane == 31) s_warp[32] = ti;
+  }
+  __syncthreads();
+  const uint64_t r = s_warp[warp] + incl - v;
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* s_warp) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_warp[warp] = v;
+  __syncthreads();
+  uint64_t t = 0;
+  if (threadIdx.x == 0) for (uint32_t w = 0; w < nw; ++w) t += s_warp[w];
+  return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ void vis_or(uint32_t* vis, uint32_t v, uint32_t bits) {
+  atomicOr(vis + (v >> 2), bits << ((v & 3u) * 8u));
+}
+
+// ------------------------------------------------------------ query set-up
+__global__ void k_set_query(DevSlot s, QueryDev qv, const int32_t* d_kw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  QueryDev q = qv;
+  if (d_kw) for (int i = 0; i < q.n_c + q.n_m; ++i) q.kw[i] = d_kw[i];
+  *s.q = q;
+  Ctl* c = s.ctl;
+  uint32_t* w = reinterpret_cast<uint32_t*>(c);
+  for (size_t i = 0; i < sizeof(Ctl) / 4; ++i) w[i] = 0;
+  c->levels[0] = c->levels[1] = -1;
+  c->last_expanded = -1;
+  *s.n_res = 0;
+}
+
+__global__ void k_run_start(DevSlot s, int run) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Ctl* c = s.ctl;
+  c->done = (run == 1 && (s.q->n_m == 0 || c->nsel == 0)) ? 1u : 0u;
+  c->work[0] = c->work[1] = 0;
+  c->nq[0] = c->nq[1] = 0;
+  c->level = 0;
+  c->last_expanded = -1;
+}
+
+// Initialisation (Section 4.2.1): keyword nodes get h = 0 and become frontiers.
+__global__ void k_seed(DevKG g, DevSlot s, int run) {
+  if (s.ctl->done) return;
+  const QueryDev& q = *s.q;
+  const int nt = run == 0 ? q.n_c : q.n_m;
+  const int kb = run == 0 ? 0 : q.n_c;
+  uint32_t beg[kMaxCols], len[kMaxCols];
+  uint32_t total = 0;
+  for (int j = 0; j < nt; ++j) {
+    const int32_t kw = q.kw[kb + j];
+    if (kw < 0 || kw >= g.n_kw) {
+      beg[j] = len[j] = 0;
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&s.ctl->err, kErrKeyword);
+      continue;
+    }
+    beg[j] = g.kw_ptr[kw];
+    len[j] = g.kw_ptr[kw + 1] - beg[j];
+    total += len[j];
+  }
+  uint32_t* F0 = s.F[0];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    uint32_t r = i;
+    int j = 0;
+    while (r >= len[j]) { r -= len[j]; ++j; }
+    const int32_t v = g.kw_nodes[beg[j] + r];
+    if (v < 0 || v >= g.n) { atomicOr(&s.ctl->err, kErrInternal); continue; }
+    s.H[size_t(v) * 8 + j] = 0;
+    vis_or(s.vis, uint32_t(v), 1u << j);
+    atomicOr(F0 + (v >> 5), 1u << (v & 31));
+  }
+}
+
+// ---------------------------------------------------------- level: enqueue
+// Frontier enqueue (Section 4.2.2): every set bit of F_l is taken and cleared.
+// Identification (Section 4.2.3): central run, a node reached by all central
+// keywords is a CG with S^c = max_j h (Theorem 3) and stops expanding;
+// marginal run with |M| >= 2, a node reached by all marginal keywords stops
+// (PTC).  Nodes still expanding become work items with their newly active
+// segment; retained nodes (an edge with a > l) are set in F_{l+1}.  Block 0
+// of the marginal run also performs the RPG identification of the level.
+// Lane = node, items compacted by warp ballots and one 64-bit atomicAdd per
+// block tile of kEnqRounds * 8 words.
+__global__ void __launch_bounds__(kEnqThreads)
+k_enqueue(DevKG g, DevSlot s, int run, int l) {
+  Ctl* c = s.ctl;
+  if (c->done) return;
+  const QueryDev& q = *s.q;
+  const int nt = run == 0 ? q.n_c : q.n_m;
+  const uint32_t full = (1u << nt) - 1u;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  constexpr uint32_t nwarp = kEnqThreads / 32;
+  uint32_t* Fc = s.F[l & 1];
+  uint32_t* Fn = s.F[(l + 1) & 1];
+  __shared__ uint64_t s_warp[33];
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_acc[kMaxK];
+
+  if (run == 1 && blockIdx.x == 0) {
+    // RPG identification: a selected CG matches when every marginal keyword
+    // has reached some node of its V_C; then S^m = max_i min_{v in V_C} h = l.
+    const uint32_t nsel = c->nsel;
+    for (uint32_t i = threadIdx.x; i < kMaxK; i += blockDim.x) s_acc[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < c->nvc; i += blockDim.x) {
+      const uint32_t p = s.vcl[i];
+      atomicOr(&s_acc[p >> kNodeBits], vis_byte(s.vis, p & kNodeMask));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t nm = 0;
+      for (uint32_t gi = 0; gi < nsel; ++gi) {
+        if (!c->matched[gi] && (s_acc[gi] & full) == full) { c->matched[gi] = 1; c->sm[gi] = uint8_t(l); }
+        nm += c->matched[gi];
+      }
+      c->n_matched = nm;
+    }
+  }
+
+  const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
+  uint32_t qcount = 0;
+  for (uint32_t tile = blockIdx.x * (nwarp * kEnqRounds); tile < nwords; tile += gridDim.x * (nwarp * kEnqRounds)) {
+    uint32_t it_node[kEnqRounds], it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
+    uint32_t my_items = 0, my_work = 0;
+#pragma unroll
+    for (int r = 0; r < kEnqRounds; ++r) {
+      it_len[r] = 0;
+      it_node[r] = 0; it_seg[r] = 0; it_msk[r] = 0;
+      const uint32_t widx = tile + r * nwarp + warp;
+      if (widx >= nwords) continue;
+      const uint32_t word = Fc[widx];
+      if (word == 0) continue;
+      if (lane == 0) Fc[widx] = 0;                // reset F for the next use
+      const uint32_t v = widx * 32 + lane;
+      const bool has = (word >> lane) & 1u;
+      qcount += has;
+      if (s.qlog && has) {
+        const uint32_t p = atomicAdd(&c->qlog_n, 1u);
+        if (p < s.qcap) s.qlog[p] = (uint32_t(l) << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
+      }
+      bool stop_now = false, expand = false, is_cg = false;
+      uint32_t cg_key = 0;
+      uint8_t eq = 0, lt = 0;
+      if (has && !((s.cf[widx] >> lane) & 1u)) {
+        const uint32_t vb = vis_byte(s.vis, v);
+        const uint2 hr = *reinterpret_cast<const uint2*>(s.H + size_t(v) * 8);
+        const uint32_t hb[2] = {hr.x, hr.y};
+        uint32_t mx = 0;
+        for (int j = 0; j < nt; ++j) {
+          if (!((vb >> j) & 1u)) continue;
+          const uint32_t h = (hb[j >> 2] >> ((j & 3) * 8)) & 0xffu;
+          mx = h > mx ? h : mx;
+          if (h == uint32_t(l)) eq |= uint8_t(1u << j);
+          else if (h < uint32_t(l)) lt |= uint8_t(1u << j);
+        }
+        if ((vb & full) == full && (run == 0 || nt >= 2)) {
+          stop_now = true;
+          s.stopl[v] = uint8_t(l);
+          if (run == 0) {
+            is_cg = true;
+            cg_key = (mx << kNodeBits) | v;
+            if (mx != uint32_t(l)) atomicOr(&c->err, kErrInternal);
+          }
+        } else {
+          expand = true;
+        }
+      }
+      const unsigned cgb = __ballot_sync(0xffffffffu, is_cg);
+      if (cgb) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&c->ncg, uint32_t(__popc(cgb)));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (is_cg) s.cg[base + __popc(cgb & ((1u << lane) - 1u))] = cg_key;
+      }
+      const unsigned stopb = __ballot_sync(0xffffffffu, stop_now);
+      if (lane == 0 && stopb) s.cf[widx] |= stopb;     // only this warp owns word widx here
+      bool retain = false;
+      if (expand) {
+        retain = g.amax[v] > uint32_t(l);
+        const uint32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
+        const uint32_t hi = seg_lower(g.adj, rb, re, uint32_t(l) + 1u);
+        const uint32_t lo = eq ? rb : seg_lower(g.adj, rb, hi, uint32_t(l));
+        if (hi > lo) {
+          it_node[r] = v; it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
+          ++my_items;
+          my_work += hi - lo;
+        }
+      }
+      const unsigned retb = __ballot_sync(0xffffffffu, retain);
+      if (lane == 0 && retb) Fn[widx] = retb;          // F_{l+1} word is zero before this level
+    }
+    // block-level compaction of the items of this tile
+    const uint64_t packed = (uint64_t(my_items) << kWorkBits) | my_work;
+    uint64_t tot = 0;
+    const uint64_t pre = block_excl_scan(packed, s_warp, &tot);
+    if (threadIdx.x == 0) s_base = tot ? atomicAdd(&c->work[l & 1], (unsigned long long)tot) : 0ull;
+    __syncthreads();
+    if (my_items) {
+      uint32_t idx = uint32_t((s_base >> kWorkBits) + (pre >> kWorkBits));
+      uint32_t off = uint32_t((s_base & kWorkMask) + (pre & kWorkMask));
+#pragma unroll
+      for (int r = 0; r < kEnqRounds; ++r) {
+        if (!it_len[r]) continue;
+        Item it;
+        it.node = it_node[r]; it.seg_begin = it_seg[r]; it.off = off;
+        it.eq = uint8_t(it_msk[r]); it.lt = uint8_t(it_msk[r] >> 8); it.pad = 0;
+        s.items[idx] = it;
+        ++idx;
+        off += it_len[r];
+      }
+    }
+    __syncthreads();
+  }
+  const uint64_t qt = block_sum(qcount, s_warp);
+  if (threadIdx.x == 0 && qt) atomicAdd(&c->nq[l & 1], uint32_t(qt));
+}
+
+// ----------------------------------------------------------- level: expand
+// Termination (every block reaches the same decision from the control block,
+// which k_enqueue finished writing) and expansion (Algorithm 1) of the work
+// items, split into tiles of kExpTile consecutive work units: a hub's
+// segment spans many tiles (grid-level split), short segments share a tile
+// (block-level), and lanes of a warp read consecutive CSR entries.
+__global__ void __launch_bounds__(kExpThreads)
+k_expand(DevKG g, DevSlot s, int run, int l) {
+  Ctl* c = s.ctl;
+  if (c->done) return;
+  const QueryDev& q = *s.q;
+  const unsigned long long wk = c->work[l & 1];
+  const uint32_t n_items = uint32_t(wk >> kWorkBits);
+  const uint32_t n_work = uint32_t(wk & kWorkMask);
+  const uint32_t nq = c->nq[l & 1];
+  const bool term = run == 0 ? (c->ncg >= uint32_t(q.k)) : (c->n_matched >= c->nsel);
+  const bool stop = (nq == 0) || term || (l >= q.L);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->level = uint32_t(l);
+    if (stop) {
+      c->done = 1;
+      c->levels[run] = (nq == 0 && l > 0) ? l - 1 : l;
+    } else {
+      c->last_expanded = l;
+      c->levels[run] = l;          // provisional; final when the run stops
+      c->work[(l + 1) & 1] = 0;
+      c->nq[(l + 1) & 1] = 0;
+    }
+  }
+  if (stop || n_work == 0) return;
+
+  __shared__ uint32_t s_off[kExpTile + 1];
+  __shared__ uint32_t s_seg[kExpTile];
+  __shared__ uint16_t s_msk[kExpTile];
+  __shared__ uint32_t s_rng[2];
+  __shared__ uint64_t s_warp[33];
+  uint32_t* Fn = s.F[(l + 1) & 1];
+  const uint32_t lv = uint32_t(l);
+  uint64_t eact = 0, hits = 0;
+  for (uint32_t t0 = blockIdx.x * kExpTile; t0 < n_work; t0 += gridDim.x * kExpTile) {
+    const uint32_t t1 = min(t0 + uint32_t(kExpTile), n_work);
+    if (threadIdx.x < 2) {
+      // last item whose offset is <= t0 (thread 0) and <= t1 - 1 (thread 1)
+      const uint32_t key = threadIdx.x == 0 ? t0 : t1 - 1;
+      uint32_t lo = 0, hi = n_items - 1;
+      while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (s.items[mid].off <= key) lo = mid; else hi = mid - 1;
+      }
+      s_rng[threadIdx.x] = lo;
+    }
+    __syncthreads();
+    const uint32_t i0 = s_rng[0], cnt = s_rng[1] - i0 + 1;   // cnt <= kExpTile (each item has work)
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const Item it = s.items[i0 + i];
+      s_off[i] = it.off; s_seg[i] = it.seg_begin;
+      s_msk[i] = uint16_t(it.eq | (uint32_t(it.lt) << 8));
+    }
+    __syncthreads();
+    uint32_t si = 0;
+    for (uint32_t u = t0 + threadIdx.x; u < t1; u += blockDim.x) {
+      uint32_t lo = si, hi = cnt - 1;                 // last s with s_off[s] <= u
+      while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
+      }
+      si = lo;
+      const uint32_t e = s_seg[si] + (u - s_off[si]);
+      const uint32_t x = __ldg(g.adj + e);
+      const uint32_t a = x >> kNodeBits;
+      const uint32_t nb = x & kNodeMask;
+      const uint32_t eq = s_msk[si] & 0xffu, lt = s_msk[si] >> 8;
+      const uint32_t act = a < lv ? eq : (eq | lt);   // columns for which the edge is new at level l
+      eact += __popc(act);
+      const uint32_t vb = vis_byte(s.vis, nb);
+      const uint32_t nw = act & ~vb;
+      if (nw) {
+        const uint32_t sh = (nb & 3u) * 8u;
+        const uint32_t old = atomicOr(s.vis + (nb >> 2), nw << sh);
+        const uint32_t won = nw & ~(old >> sh) & 0xffu;
+        if (won) {
+          for (uint32_t m = won; m; m &= m - 1) s.H[size_t(nb) * 8 + (__ffs(m) - 1)] = uint8_t(lv + 1);
+          atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
+          hits += __popc(won);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const uint64_t te = block_sum(eact, s_warp);
+  const uint64_t th = block_sum(hits, s_warp);
+  if (threadIdx.x == 0) {
+    if (te) atomicAdd(&c->e_act[run], (unsigned long long)te);
+    if (th) atomicAdd(&c->hits[run], (unsigned long long)th);
+  }
+}
+
+// ------------------------------------------------------ top-w CG selection
+// Block-local top-K merge: each block sorts a chunk of up to kTopkChunk keys
+// in shared memory (bitonic) and keeps its K smallest; passes repeat on the
+// survivors.  Keys are (level << 26) | node, so ascending order is the
+// (S^c, node id) order of the selection; 0xffffffff pads short chunks.
+__global__ void __launch_bounds__(kTopkThreads)
+k_topk_pass(DevSlot s, int pass) {
+  Ctl* c = s.ctl;
+  const uint32_t K = uint32_t(s.q->k);
+  const uint32_t* src = pass == 0 ? s.cg : s.topk[(pass - 1) & 1];
+  const uint32_t n_in = pass == 0 ? c->ncg : c->topk_n[(pass - 1) & 1];
+  uint32_t* dst = s.topk[pass & 1];
+  const bool sorted_in = pass > 0 && n_in <= K;
+  const uint32_t nchunks = sorted_in ? 1 : (n_in + kTopkChunk - 1) / kTopkChunk;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->topk_n[pass & 1] = sorted_in ? n_in : min(n_in, nchunks * K);
+  if (sorted_in) {                     // already reduced: copy through
+    if (blockIdx.x == 0) for (uint32_t i = threadIdx.x; i < n_in; i += blockDim.x) dst[i] = src[i];
+    return;
+  }
+  __shared__ uint32_t key[kTopkChunk];
+  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const uint32_t b = ch * kTopkChunk;
+    const uint32_t len = min(uint32_t(kTopkChunk), n_in - b);
+    for (uint32_t i = threadIdx.x; i < kTopkChunk; i += blockDim.x) key[i] = i < len ? src[b + i] : 0xffffffffu;
+    __syncthreads();
+    for (uint32_t k = 2; k <= kTopkChunk; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < kTopkChunk; i += blockDim.x) {
+          const uint32_t p = i ^ j;
+          if (p > i) {
+            const uint32_t a = key[i], bb = key[p];
+            const bool up = (i & k) == 0;
+            if ((a > bb) == up) { key[i] = bb; key[p] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    const uint32_t keep = min(K, len);
+    for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) dst[ch * K + i] = i < keep ? key[i] : 0xffffffffu;
+    __syncthreads();
+  }
+}
+
+__global__ void k_select(DevSlot s, int last_pass) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Ctl* c = s.ctl;
+  const uint32_t K = uint32_t(s.q->k);
+  const uint32_t* src = s.topk[last_pass & 1];
+  const uint32_t n = min(c->topk_n[last_pass & 1], K);
+  uint32_t ns = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t key = src[i];
+    if (key == 0xffffffffu) break;
+    c->sel[ns] = int32_t(key & kNodeMask);
+    c->sel_sc[ns] = uint8_t(key >> kNodeBits);
+    ++ns;
+  }
+  c->nsel = ns;
+}
+
+// ---------------------------------------------------------------- recovery
+// Recovering phase (Algorithm 2) for all selected CGs at once, one block.
+// For each central column j a backward sweep from the CG nodes, level by
+// level downwards, follows the edges n -> q with h_q = max(a, h_n) + 1
+// (tight, Lemma 3) whose source n was still expanding at level max(a, h_n)
+// (it had not stopped earlier).  Each node carries a bit mask of the CGs it
+// belongs to, OR-ed along the tight edges; the union over columns gives V^c
+// per CG, and V_C are the nodes of V^c that hold a central keyword.
+__global__ void __launch_bounds__(kRecThreads)
+k_recover(DevKG g, DevSlot s) {
+  Ctl* c = s.ctl;
+  const QueryDev& q = *s.q;
+  const uint32_t nsel = c->nsel;
+  if (nsel == 0 || q.n_m == 0) return;   // V_C is only needed by the marginal run
+  const int nc = q.n_c;
+  const int maxlev = c->levels[0];
+  __shared__ uint32_t s_off[kRecThreads];
+  __shared__ uint32_t s_rb[kRecThreads];
+  __shared__ unsigned long long s_m[kRecThreads];
+  __shared__ uint64_t s_warp[33];
+  __shared__ uint32_t s_cnt, s_total;
+  if (threadIdx.x == 0) { c->ulist_n = 0; c->nvc = 0; }
+  __syncthreads();
+  for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
+    const uint32_t v = uint32_t(c->sel[gi]);
+    const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
+    if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < nc; ++j) {
+    if (threadIdx.x == 0) c->rlist_n = 0;
+    __syncthreads();
+    for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
+      const uint32_t v = uint32_t(c->sel[gi]);
+      if (s.H[size_t(v) * 8 + j] == 0) continue;      // the CG node holds keyword j
+      const unsigned long long old = atomicOr(&s.rmask[v], 1ull << gi);
+      if (old == 0) s.rlist[atomicAdd(&c->rlist_n, 1u)] = v;
+    }
+    __syncthreads();
+    for (int x = maxlev; x >= 1; --x) {
+      if (threadIdx.x == 0) s_cnt = c->rlist_n;
+      __syncthreads();
+      const uint32_t cnt = s_cnt;
+      for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
+        const uint32_t i = c0 + threadIdx.x;
+        uint32_t len = 0, qn = 0, rb = 0;
+        unsigned long long m = 0;
+        if (i < cnt) {
+          qn = s.rlist[i];
+          if (s.H[size_t(qn) * 8 + j] == uint8_t(x)) {
+            rb = g.row_ptr[qn];
+            len = seg_lower(g.adj, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
+            m = s.rmask[qn];
+          }
+        }
+        uint64_t tot = 0;
+        const uint32_t pre = uint32_t(block_excl_scan(len, s_warp, &tot));
+        s_off[threadIdx.x] = pre; s_rb[threadIdx.x] = rb; s_m[threadIdx.x] = m;
+        if (threadIdx.x == 0) s_total = uint32_t(tot);
+        __syncthreads();
+        const uint32_t total = s_total;
+        for (uint32_t u = threadIdx.x; u < total; u += blockDim.x) {
+          uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u and work
+          while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+            if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
+          }
+          const uint32_t e = s_rb[lo] + (u - s_off[lo]);
+          const uint32_t xe = __ldg(g.adj + e);
+          const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
+          if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
+          const uint32_t hn = s.H[size_t(nb) * 8 + j];
+          const uint32_t lam = a > hn ? a : hn;
+          if (lam + 1 != uint32_t(x)) continue;                     // not tight
+          if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
+          const unsigned long long old = atomicOr(&s.rmask[nb], s_m[lo]);
+          if (old == 0) {
+            const uint32_t p = atomicAdd(&c->rlist_n, 1u);
+            if (p < s.cap) s.rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // fold column j into the union masks and clear the column masks
+    for (uint32_t i = threadIdx.x; i < c->rlist_n; i += blockDim.x) {
+      const uint32_t v = s.rlist[i];
+      const unsigned long long m = s.rmask[v];
+      s.rmask[v] = 0;
+      const unsigned long long old = atomicOr(&s.vmask[v], m);
+      if (old == 0) {
+        const uint32_t p = atomicAdd(&c->ulist_n, 1u);
+        if (p < s.cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
+      }
+    }
+    __syncthreads();
+  }
+  // V_C: nodes of V^c holding a central keyword (h == 0 in a central column)
+  const uint32_t nu = c->ulist_n;
+  for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) {
+    const uint32_t v = s.ulist[i];
+    unsigned long long m = s.vmask[v];
+    s.vmask[v] = 0;
+    const uint32_t vb = vis_byte(s.vis, v);
+    bool holds = false;
+    for (int j = 0; j < nc; ++j) holds |= ((vb >> j) & 1u) && s.H[size_t(v) * 8 + j] == 0;
+    if (!holds) continue;
+    for (; m; m &= m - 1) {
+      const uint32_t gi = __ffsll(m) - 1;
+      const uint32_t p = atomicAdd(&c->nvc, 1u);
+      if (p < s.cap) s.vcl[p] = (gi << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
+    }
+  }
+}
+
+// --------------------------------------------------------------- results
+// Eq. 6 scores and the top-k by (S^r, node id).  With M empty the results
+// are the selected CGs with S^m = 0 and S^r = S^c.
+__global__ void k_results(DevSlot s) {
+  Ctl* c = s.ctl;
+  const QueryDev& q = *s.q;
+  rpq_result* out = reinterpret_cast<rpq_result*>(s.res);
+  const uint32_t nsel = c->nsel;
+  __shared__ double s_sr[kMaxK];
+  __shared__ uint32_t s_ok[kMaxK];
+  const uint32_t gi = threadIdx.x;
+  if (gi < kMaxK) {
+    s_ok[gi] = 0;
+    if (gi < nsel) {
+      if (q.n_m == 0) { s_ok[gi] = 1; s_sr[gi] = double(c->sel_sc[gi]); }
+      else if (c->matched[gi]) {
+        s_ok[gi] = 1;
+        s_sr[gi] = q.gamma * double(c->sel_sc[gi]) + (1.0 - q.gamma) * double(c->sm[gi]);
+      }
+    }
+  }
+  __syncthreads();
+  if (gi < nsel && s_ok[gi]) {
+    const int32_t node = c->sel[gi];
+    uint32_t rank = 0;
+    for (uint32_t o = 0; o < nsel; ++o) {
+      if (!s_ok[o] || o == gi) continue;
+      if (s_sr[o] < s_sr[gi] || (s_sr[o] == s_sr[gi] && c->sel[o] < node)) ++rank;
+    }
+    if (rank < uint32_t(q.k)) {
+      rpq_result r;
+      r.node = node;
+      r.s_c = c->sel_sc[gi];
+      r.s_m = q.n_m == 0 ? 0 : c->sm[gi];
+      r.reserved = 0;
+      r.s_r = s_sr[gi];
+      out[rank] = r;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t n = 0;
+    for (uint32_t o = 0; o < nsel; ++o) n += s_ok[o];
+    n = min(n, uint32_t(q.k));
+    c->n_res = n;
+    *s.n_res = int32_t(n);
+    if (c->err) atomicOr(s.sticky, c->err);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+constexpr int kTopkPasses = 4;
+
+int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st) {
+  k_set_query<<<1, 32, 0, st>>>(s, qv, d_kw);
+  return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
+}
+
+// Launch one run (seed + L+1 levels).  nt = number of columns of the run.
+static void launch_run(const DevKG& g, const DevSlot& s, int run, int L, cudaStream_t st) {
+  const size_t nwords = (size_t(g.n) + 31) / 32;
+  k_run_start<<<1, 32, 0, st>>>(s, run);
+  cudaMemsetAsync(s.vis, 0, ((size_t(g.n) + 3) / 4) * 4, st);
+  cudaMemsetAsync(s.F[0], 0, nwords * 4, st);
+  cudaMemsetAsync(s.F[1], 0, nwords * 4, st);
+  cudaMemsetAsync(s.cf, 0, nwords * 4, st);
+  const int sms = num_sms();
+  k_seed<<<sms * 2, 256, 0, st>>>(g, s, run);
+  const int enq_blocks = int(std::min<size_t>(size_t(sms) * 8, (nwords + 31) / 32 + 1));
+  for (int l = 0; l <= L; ++l) {
+    k_enqueue<<<enq_blocks, kEnqThreads, 0, st>>>(g, s, run, l);
+    k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, l);
+  }
+}
+
+int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st) {
+  launch_run(g, s, 0, L, st);
+  const int sms = num_sms();
+  for (int p = 0; p < kTopkPasses; ++p) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, p);
+  k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+  return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
+}
+
+int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st) {
+  if (n_m > 0) {
+    k_recover<<<1, kRecThreads, 0, st>>>(g, s);
+    launch_run(g, s, 1, L, st);
+  }
+  k_results<<<1, kMaxK, 0, st>>>(s);
+  return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
+}
+
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st) {
+  const int rc = launch_central_part(g, s, L, st);
+  if (rc != RPQ_OK) return rc;
+  return launch_marginal_part(g, s, n_m, L, st);
+}
+
+}  // namespace rpq
