@@ -1,0 +1,241 @@
+"""Python binding of librpq: radial-pattern keyword search on a B300 GPU.
+
+Argument marshalling only.  Every step of the search runs in the CUDA
+kernels of ``librpq.so`` (built from ``csrc/`` for sm_103a); there is no
+CPU path.  If the library cannot be loaded the import of this binding's
+functions raises.
+
+Typical use::
+
+    kg = KG(row_ptr, col, label, n_labels, kw_ptr, kw_nodes, alpha=0.5, abar=3.3)
+    res, stats = kg.search(central=[12, 40], marginal=[7], k=20, max_depth=8)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+RPQ_OK, RPQ_EINVAL, RPQ_ENOMEM, RPQ_ETIMEOUT, RPQ_ECUDA, RPQ_ELIMIT, RPQ_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
+INF = 255
+SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
+           "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_strerror", "rpq_last_error"]
+
+
+class RPQError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class KGDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m2", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("label", ctypes.c_void_p), ("n_labels", ctypes.c_int32),
+                ("n_kw", ctypes.c_int32), ("kw_ptr", ctypes.c_void_p), ("kw_nodes", ctypes.c_void_p),
+                ("alpha", ctypes.c_double), ("abar", ctypes.c_double)]
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("central", ctypes.c_void_p), ("n_c", ctypes.c_int32), ("marginal", ctypes.c_void_p),
+                ("n_m", ctypes.c_int32), ("k", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("gamma", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("e_act_central", ctypes.c_int64), ("e_act_marginal", ctypes.c_int64),
+                ("hits_central", ctypes.c_int64), ("hits_marginal", ctypes.c_int64),
+                ("levels_central", ctypes.c_int32), ("levels_marginal", ctypes.c_int32),
+                ("n_cg", ctypes.c_int32), ("n_selected", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TraceBuf(ctypes.Structure):
+    _fields_ = [("h_central", ctypes.c_void_p), ("h_marginal", ctypes.c_void_p),
+                ("frontier_c_ptr", ctypes.c_void_p), ("frontier_c", ctypes.c_void_p),
+                ("frontier_c_cap", ctypes.c_int64), ("frontier_c_levels", ctypes.c_int32),
+                ("frontier_m_ptr", ctypes.c_void_p), ("frontier_m", ctypes.c_void_p),
+                ("frontier_m_cap", ctypes.c_int64), ("frontier_m_levels", ctypes.c_int32),
+                ("cgs", ctypes.c_void_p), ("cg_cap", ctypes.c_int64), ("n_cgs", ctypes.c_int64),
+                ("vc", ctypes.c_void_p), ("vc_cap", ctypes.c_int64), ("n_vc", ctypes.c_int64),
+                ("selected", ctypes.c_int32 * MAX_K), ("n_selected", ctypes.c_int32)]
+
+
+RESULT_DTYPE = np.dtype([("node", np.int32), ("s_c", np.int32), ("s_m", np.int32), ("reserved", np.int32),
+                         ("s_r", np.float64)])
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load librpq.so, building it first when sources are newer."""
+    global _lib
+    if _lib is None:
+        if _build.stale():
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.rpq_load_kg.argtypes = [ctypes.POINTER(KGDesc), ctypes.POINTER(P)]
+        L.rpq_free_kg.argtypes = [P]
+        L.rpq_kg_export.argtypes = [P, P, P]
+        L.rpq_kg_info.argtypes = [P, P, P, P]
+        L.rpq_search.argtypes = [P, ctypes.POINTER(Query), P, P, P]
+        L.rpq_search_batch.argtypes = [P, P, i32, P, P, P, P]
+        L.rpq_trace.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(TraceBuf)]
+        L.rpq_search_device.argtypes = [P, P, i32, i32, i32, i32, f64, P, P]
+        L.rpq_sync_device.argtypes = [P]
+        L.rpq_strerror.argtypes = [ctypes.c_int]
+        L.rpq_strerror.restype = ctypes.c_char_p
+        L.rpq_last_error.restype = ctypes.c_char_p
+        for f in SYMBOLS[:-2]:
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != RPQ_OK:
+        raise RPQError(rc, lib().rpq_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class QuerySpec:
+    central: list
+    marginal: list
+    k: int
+    max_depth: int
+    gamma: float = 0.5
+
+
+def _query(central, marginal, k, max_depth, gamma, keep):
+    c = np.ascontiguousarray(central, np.int32)
+    m = np.ascontiguousarray(marginal, np.int32)
+    keep.extend([c, m])
+    return Query(_ptr(c), len(c), _ptr(m) if len(m) else None, len(m), int(k), int(max_depth), float(gamma))
+
+
+class KG:
+    """A knowledge graph resident on the current CUDA device."""
+
+    def __init__(self, row_ptr, col, label, n_labels, kw_ptr, kw_nodes, alpha=0.5, abar=3.0):
+        self._h = ctypes.c_void_p()
+        self._keep = [np.ascontiguousarray(row_ptr, np.int64), np.ascontiguousarray(col, np.int32),
+                      np.ascontiguousarray(label, np.uint16), np.ascontiguousarray(kw_ptr, np.int64),
+                      np.ascontiguousarray(kw_nodes, np.int32)]
+        rp, cl, lb, kp, kn = self._keep
+        self.n = len(rp) - 1
+        self.m2 = int(rp[-1])
+        d = KGDesc(self.n, self.m2, _ptr(rp), _ptr(cl), _ptr(lb), int(n_labels), len(kp) - 1, _ptr(kp), _ptr(kn),
+                   float(alpha), float(abar))
+        _check(lib().rpq_load_kg(ctypes.byref(d), ctypes.byref(self._h)))
+        self._keep = None
+
+    @classmethod
+    def from_dataset(cls, ds):
+        g = ds.graph
+        return cls(g.row_ptr, g.col, g.label, g.n_labels, ds.kw_ptr, ds.kw_nodes, ds.alpha, ds.abar)
+
+    def close(self):
+        if self._h:
+            lib().rpq_free_kg(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, m2, b = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().rpq_kg_info(self._h, ctypes.byref(n), ctypes.byref(m2), ctypes.byref(b)))
+        return dict(n=n.value, m2=m2.value, device_bytes=b.value)
+
+    def export(self):
+        """Packed adjacency ((level << 26) | neighbour, rows ascending) and amax."""
+        adj = np.empty(self.m2, np.uint32)
+        amax = np.empty(self.n, np.uint8)
+        _check(lib().rpq_kg_export(self._h, _ptr(adj), _ptr(amax)))
+        return adj, amax
+
+    def search(self, central, marginal, k, max_depth, gamma=0.5):
+        keep = []
+        q = _query(central, marginal, k, max_depth, gamma, keep)
+        out = np.zeros(max(int(k), 1), RESULT_DTYPE)
+        n_out = ctypes.c_int32()
+        st = Stats()
+        _check(lib().rpq_search(self._h, ctypes.byref(q), _ptr(out), ctypes.byref(n_out), ctypes.byref(st)))
+        return out[:n_out.value].copy(), st.as_dict()
+
+    def search_batch(self, queries):
+        """queries: iterable of objects with central, marginal, k, max_depth
+        (and optionally gamma).  Returns a list of (results, stats, status)."""
+        queries = list(queries)
+        keep = []
+        arr = (Query * max(len(queries), 1))()
+        for i, qs in enumerate(queries):
+            arr[i] = _query(qs.central, qs.marginal, qs.k, qs.max_depth, getattr(qs, "gamma", 0.5), keep)
+        ks = [int(q.k) for q in queries]
+        base = np.concatenate([[0], np.cumsum(ks)]).astype(np.int64)
+        out = np.zeros(max(int(base[-1]), 1), RESULT_DTYPE)
+        n_out = np.zeros(max(len(queries), 1), np.int32)
+        status = np.zeros(max(len(queries), 1), np.int32)
+        st = (Stats * max(len(queries), 1))()
+        _check(lib().rpq_search_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(queries), _ptr(out),
+                                      _ptr(n_out), _ptr(status), ctypes.cast(st, ctypes.c_void_p)))
+        return [(out[base[i]:base[i] + n_out[i]].copy(), st[i].as_dict(), int(status[i])) for i in range(len(queries))]
+
+    def trace(self, central, marginal, k, max_depth, gamma=0.5, frontier_cap=None):
+        """Search one query and return its intermediate state for inspection."""
+        keep = []
+        q = _query(central, marginal, k, max_depth, gamma, keep)
+        nc, nm = len(central), len(marginal)
+        cap = frontier_cap or self.n * (max_depth + 1)
+        hc = np.empty((self.n, nc), np.uint8)
+        hm = np.empty((self.n, max(nm, 1)), np.uint8)
+        fcp = np.zeros(MAX_LEVEL + 2, np.int64)
+        fmp = np.zeros(MAX_LEVEL + 2, np.int64)
+        fc = np.empty(cap, np.int32)
+        fm = np.empty(cap, np.int32)
+        cgs = np.empty(self.n, np.int64)
+        vc = np.empty(self.n * 4, np.int64)
+        tb = TraceBuf(_ptr(hc), _ptr(hm) if nm else None, _ptr(fcp), _ptr(fc), cap, 0, _ptr(fmp), _ptr(fm), cap, 0,
+                      _ptr(cgs), len(cgs), 0, _ptr(vc), len(vc), 0)
+        out = np.zeros(max(int(k), 1), RESULT_DTYPE)
+        n_out = ctypes.c_int32()
+        st = Stats()
+        _check(lib().rpq_trace(self._h, ctypes.byref(q), _ptr(out), ctypes.byref(n_out), ctypes.byref(st),
+                               ctypes.byref(tb)))
+        fr_c = [fc[fcp[l]:fcp[l + 1]].copy() for l in range(tb.frontier_c_levels)]
+        fr_m = [fm[fmp[l]:fmp[l + 1]].copy() for l in range(tb.frontier_m_levels)]
+        vcs = vc[:tb.n_vc]
+        nsel = tb.n_selected
+        return dict(results=out[:n_out.value].copy(), stats=st.as_dict(), h_central=hc,
+                    h_marginal=hm[:, :nm] if nm else None, frontiers_central=fr_c, frontiers_marginal=fr_m,
+                    cgs=cgs[:tb.n_cgs].copy(), selected=np.array(tb.selected[:nsel], np.int64),
+                    vc=[np.sort(vcs[(vcs >> 26) == g] & ((1 << 26) - 1)) for g in range(nsel)])
+
+    def search_device(self, d_keywords: int, n_c: int, n_m: int, k: int, max_depth: int, gamma: float,
+                      d_out: int, d_n_out: int):
+        """Enqueue a search whose keyword ids (int32) and outputs live in
+        device memory (raw device pointers, e.g. ``tensor.data_ptr()``)."""
+        _check(lib().rpq_search_device(self._h, ctypes.c_void_p(d_keywords), n_c, n_m, k, max_depth, gamma,
+                                       ctypes.c_void_p(d_out), ctypes.c_void_p(d_n_out)))
+
+    def sync_device(self):
+        _check(lib().rpq_sync_device(self._h))

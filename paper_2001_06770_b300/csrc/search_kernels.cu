@@ -175,7 +175,8 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
     const uint32_t nsel = c->nsel;
     for (uint32_t i = threadIdx.x; i < kMaxK; i += blockDim.x) s_acc[i] = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < c->nvc; i += blockDim.x) {
+    const uint32_t nvc = min(c->nvc, s.cap);
+    for (uint32_t i = threadIdx.x; i < nvc; i += blockDim.x) {
       const uint32_t p = s.vcl[i];
       atomicOr(&s_acc[p >> kNodeBits], vis_byte(s.vis, p & kNodeMask));
     }
@@ -486,7 +487,7 @@ k_recover(DevKG g, DevSlot s) {
     }
     __syncthreads();
     for (int x = maxlev; x >= 1; --x) {
-      if (threadIdx.x == 0) s_cnt = c->rlist_n;
+      if (threadIdx.x == 0) s_cnt = min(c->rlist_n, s.cap);
       __syncthreads();
       const uint32_t cnt = s_cnt;
       for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
@@ -531,7 +532,8 @@ k_recover(DevKG g, DevSlot s) {
       }
     }
     // fold column j into the union masks and clear the column masks
-    for (uint32_t i = threadIdx.x; i < c->rlist_n; i += blockDim.x) {
+    const uint32_t nr = min(c->rlist_n, s.cap);
+    for (uint32_t i = threadIdx.x; i < nr; i += blockDim.x) {
       const uint32_t v = s.rlist[i];
       const unsigned long long m = s.rmask[v];
       s.rmask[v] = 0;
@@ -544,7 +546,7 @@ k_recover(DevKG g, DevSlot s) {
     __syncthreads();
   }
   // V_C: nodes of V^c holding a central keyword (h == 0 in a central column)
-  const uint32_t nu = c->ulist_n;
+  const uint32_t nu = min(c->ulist_n, s.cap);
   for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) {
     const uint32_t v = s.ulist[i];
     unsigned long long m = s.vmask[v];
