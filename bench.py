@@ -1,0 +1,326 @@
+"""Benchmark of the B300 radial-pattern keyword search (one JSON line on stdout).
+
+Workload (N = 1): the medium synthetic knowledge graph - R-MAT
+(a=.57, b=.19, c=.19), 2^21 nodes, 2^25 sampled edges, int32 CSR both
+directions - with 64 queries issued one at a time (|C| in 2..4, |M| in 0..4,
+keyword ranks 100..20,000, k = 20, max depth 8).  One step = the 64 queries.
+
+  value      queries/s with the query keyword ids already in device memory and
+             results left there (rpq_search_device, CUDA graph per shape),
+             CUDA events on the library's stream, L2 flushed between steps
+  e2e        the same through rpq_search (host buffers in and out, one
+             synchronous call per query), wall clock
+  roofline   the expansion kernel: algorithmic bytes / its device time,
+             measured with CUDA events around each launch (profiling pass)
+  cpu_baseline  the serial CPU oracle on a bounded sample of the workload
+
+``--impl reference`` times the CPU oracle itself as the reference arm.
+Multi-GPU (torchrun): queries are independent, every rank runs its own copy
+of the workload on its GPU (replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RPQ queries/sec and GTEPS (batched vs one-at-a-time, bit-exact); p50/p99 latency"
+WORKLOAD = ("medium: R-MAT(.57,.19,.19) 2^21 nodes, 2^25 sampled edges, symmetric int32 CSR; "
+            "64 RPQs one at a time, |C| 2-4, |M| 0-4, ranks 100-20000, k=20, L=8")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6400.0
+# DRAM bytes per expansion launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the kernel source with this SHA-1 prefix; the
+# value is reported only while the kernel source is unchanged.
+NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+
+
+def kernels_per_query(n_m: int, L: int) -> int:
+    """Kernels one query launches (same count as the library's launch list)."""
+    run = 2 + 2 * (L + 1)
+    return 1 + run + 4 + 1 + ((1 + run) if n_m > 0 else 0) + 1
+
+
+def hbm_peak():
+    try:
+        pk = json.load(open(PEAKS_FILE))
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 6:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = max(mx, float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[2:6]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(ds, qs, n, act=None):
+    """Serial oracle on the first n queries: (queries/s, seconds, n)."""
+    import oracle
+    if act is None:
+        act = oracle.dataset_activation(ds)
+    t = time.perf_counter()
+    for q in qs[:n]:
+        oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    dt = time.perf_counter() - t
+    return n / dt, dt, n
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    import oracle
+    import rpqgen
+    ds = rpqgen.make_dataset("medium")
+    qs = rpqgen.workload_queries("medium", ds)
+    act = oracle.dataset_activation(ds)
+    times = []
+    for s in range(args.warmup + args.steps):
+        q = qs[s % len(qs)]
+        t = time.perf_counter()
+        oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    total = sum(times)
+    qps = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one query of the workload (cycling)"},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} queries of the 64, serial C oracle, one core"},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    ws, rank, local = dist_init()
+    import torch
+    import paper_2001_06770_b300 as rpq
+    import rpqgen
+
+    torch.cuda.set_device(local)
+    ds = rpqgen.make_dataset("medium")
+    qs = rpqgen.workload_queries("medium", ds)
+    nq = len(qs)
+    kg = rpq.KG.from_dataset(ds)
+    stream = torch.cuda.ExternalStream(kg.slot_stream(0))
+    # device-resident inputs and outputs
+    kw_dev = [torch.tensor(list(q.central) + list(q.marginal), dtype=torch.int32, device="cuda") for q in qs]
+    out_dev = torch.zeros((nq, 64 * 24), dtype=torch.uint8, device="cuda")
+    nout_dev = torch.zeros(nq, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MB > 126 MB L2
+    torch.cuda.synchronize()
+
+    def step_device():
+        for i, q in enumerate(qs):
+            kg.search_device(kw_dev[i].data_ptr(), len(q.central), len(q.marginal), q.k, q.max_depth, q.gamma,
+                             out_dev[i].data_ptr(), nout_dev[i:].data_ptr())
+
+    # per-query statistics (E_act etc.) and correctness of the device path
+    stats = []
+    host_res = []
+    for q in qs:
+        r, st = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        stats.append(st)
+        host_res.append(r)
+    e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
+    launches_per_step = sum(kernels_per_query(len(q.marginal), q.max_depth) for q in qs)
+
+    for _ in range(args.warmup):
+        step_device()
+    kg.sync_device()
+    for i in range(nq):   # device path returns the host path's results
+        got = np.frombuffer(out_dev[i].cpu().numpy().tobytes()[:24 * int(nout_dev[i].item())], rpq.RESULT_DTYPE)
+        assert got.tobytes() == host_res[i].tobytes(), f"device/host mismatch on query {i}"
+
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    step_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()                       # L2 flush, outside the timed events
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step_device()
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    kg.sync_device()
+    t_dev = allmax(ws, sum(step_ms) / 1e3)
+    value = ws * nq * args.steps / t_dev
+
+    # end to end through the host API: keyword ids in, results out, per call
+    lat = []
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for q in qs:
+            t = time.perf_counter()
+            kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+            lat.append(time.perf_counter() - t)
+    t_e2e = allmax(ws, time.perf_counter() - t0)
+    e2e = ws * nq * args.steps / t_e2e
+    h2d = 88 * nq                                  # parameter block with the keyword ids, per query
+    d2h = sum(24 * q.k + 600 for q in qs)          # results + control block (600 B), per query
+
+    # batched: all 64 queries in one rpq_search_batch call (concurrent slots)
+    kg.search_batch(qs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        kg.search_batch(qs)
+    t_b = allmax(ws, time.perf_counter() - t0)
+    batched = ws * nq * args.steps / t_b
+
+    # profiling pass: device time of each kernel class (events around launches)
+    kg.set_profiling(True)
+    for q in qs:
+        kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    prof = kg.profile(reset=True)
+    kg.set_profiling(False)
+    exp_ms, exp_launches = prof["expand"]
+    units = sum(s["work_units"] for s in stats)
+    items = sum(s["work_items"] for s in stats)
+    hits = sum(s["hits_central"] + s["hits_marginal"] for s in stats)
+    alg_bytes = 4 * units + e_act + 2 * hits + 16 * items      # adjacency, level checks, writes, items
+    achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
+    peak, peak_kind = hbm_peak()
+    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2001_06770_b300", "csrc", "search_kernels.cu"),
+                                "rb").read()).hexdigest()[:12]
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == src_sha else None
+
+    if rank != 0:
+        return 0
+    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    total_ms = sum(v[0] for v in prof.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "gteps": e_act * ws * args.steps / t_dev / 1e9,
+        "e_act_per_step": e_act,
+        "batched_qps": batched,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+        "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes / max(exp_launches, 1),
+                     "avg_launch_us": 1e3 * exp_ms / max(exp_launches, 1), "launches": exp_launches,
+                     "share_of_device_time": exp_ms / total_ms if total_ms else None},
+        "kernel_ms_per_step": {k: v[0] for k, v in prof.items()},
+        "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {cpu_n} of the 64 queries, serial C oracle, {cpu_s:.1f} s"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    kg.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rpq", choices=["rpq", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

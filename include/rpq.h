@@ -138,6 +138,9 @@ typedef struct {
     int32_t levels_marginal;
     int32_t n_cg;           /* CGs identified in the central run */
     int32_t n_selected;     /* CGs kept (top-w) */
+    int64_t work_units;     /* CSR entries read by the expansions (both runs) */
+    int64_t work_items;     /* (frontier node, level) expansion items */
+    int64_t frontier_nodes; /* sum over levels of |Q_l| (both runs) */
 } rpq_stats;
 
 /* Search one query (Sections 3-4): central run -> top-w CGs -> recovery of
@@ -216,6 +219,26 @@ int rpq_search_device(rpq_kg *kg, const int32_t *d_keywords, int32_t n_c, int32_
 /* Wait for searches issued with rpq_search_device and report the first
  * device-side error since the previous call. */
 int rpq_sync_device(rpq_kg *kg);
+
+/* ------------------------------------------------------------- profiling */
+/* CUDA stream (a cudaStream_t) on which search slot `slot` runs its kernels;
+ * slot 0 serves rpq_search, rpq_trace and rpq_search_device.  The slot is
+ * created if needed.  Useful to time searches with CUDA events. */
+int rpq_slot_stream(rpq_kg *kg, int32_t slot, void **stream);
+
+/* Kernel timing.  While enabled, searches launch their kernels directly (no
+ * CUDA graph) and bracket each launch with CUDA events; rpq_profile_read
+ * returns the accumulated device milliseconds and launch counts per kernel
+ * class and, with reset != 0, clears them. */
+enum { RPQ_PROF_SETUP = 0, RPQ_PROF_ENQUEUE, RPQ_PROF_EXPAND, RPQ_PROF_TOPK, RPQ_PROF_RECOVER,
+       RPQ_PROF_RESULTS, RPQ_PROF_CLASSES };
+typedef struct {
+    double ms[RPQ_PROF_CLASSES];
+    int64_t launches[RPQ_PROF_CLASSES];
+} rpq_profile;
+
+int rpq_set_profiling(rpq_kg *kg, int32_t enable);
+int rpq_profile_read(rpq_kg *kg, rpq_profile *out, int32_t reset);
 
 /* -------------------------------------------------------------- messages */
 const char *rpq_strerror(int code);

@@ -27,7 +27,9 @@ RPQ_OK, RPQ_EINVAL, RPQ_ENOMEM, RPQ_ETIMEOUT, RPQ_ECUDA, RPQ_ELIMIT, RPQ_EINTERN
 MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
-           "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_strerror", "rpq_last_error"]
+           "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
+           "rpq_profile_read", "rpq_strerror", "rpq_last_error"]
+PROF_CLASSES = ["setup", "enqueue", "expand", "topk", "recover", "results"]
 
 
 class RPQError(RuntimeError):
@@ -53,7 +55,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("e_act_central", ctypes.c_int64), ("e_act_marginal", ctypes.c_int64),
                 ("hits_central", ctypes.c_int64), ("hits_marginal", ctypes.c_int64),
                 ("levels_central", ctypes.c_int32), ("levels_marginal", ctypes.c_int32),
-                ("n_cg", ctypes.c_int32), ("n_selected", ctypes.c_int32)]
+                ("n_cg", ctypes.c_int32), ("n_selected", ctypes.c_int32),
+                ("work_units", ctypes.c_int64), ("work_items", ctypes.c_int64), ("frontier_nodes", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -68,6 +71,10 @@ class TraceBuf(ctypes.Structure):
                 ("cgs", ctypes.c_void_p), ("cg_cap", ctypes.c_int64), ("n_cgs", ctypes.c_int64),
                 ("vc", ctypes.c_void_p), ("vc_cap", ctypes.c_int64), ("n_vc", ctypes.c_int64),
                 ("selected", ctypes.c_int32 * MAX_K), ("n_selected", ctypes.c_int32)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
 
 RESULT_DTYPE = np.dtype([("node", np.int32), ("s_c", np.int32), ("s_m", np.int32), ("reserved", np.int32),
@@ -95,6 +102,9 @@ def lib():
         L.rpq_trace.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(TraceBuf)]
         L.rpq_search_device.argtypes = [P, P, i32, i32, i32, i32, f64, P, P]
         L.rpq_sync_device.argtypes = [P]
+        L.rpq_slot_stream.argtypes = [P, i32, ctypes.POINTER(P)]
+        L.rpq_set_profiling.argtypes = [P, i32]
+        L.rpq_profile_read.argtypes = [P, ctypes.POINTER(Profile), i32]
         L.rpq_strerror.argtypes = [ctypes.c_int]
         L.rpq_strerror.restype = ctypes.c_char_p
         L.rpq_last_error.restype = ctypes.c_char_p
@@ -239,3 +249,18 @@ class KG:
 
     def sync_device(self):
         _check(lib().rpq_sync_device(self._h))
+
+    def slot_stream(self, slot: int = 0) -> int:
+        """Raw cudaStream_t of a search slot (for CUDA-event timing)."""
+        st = ctypes.c_void_p()
+        _check(lib().rpq_slot_stream(self._h, slot, ctypes.byref(st)))
+        return st.value or 0
+
+    def set_profiling(self, enable: bool):
+        _check(lib().rpq_set_profiling(self._h, int(bool(enable))))
+
+    def profile(self, reset: bool = False):
+        """Accumulated device ms and launch counts per kernel class."""
+        p = Profile()
+        _check(lib().rpq_profile_read(self._h, ctypes.byref(p), int(bool(reset))))
+        return {c: (p.ms[i], p.launches[i]) for i, c in enumerate(PROF_CLASSES)}

@@ -13,9 +13,9 @@
 namespace rpq {
 
 int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st);
-int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st);
-int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st);
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
+int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof);
+int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
 
 static thread_local std::string g_last_error;
 
@@ -169,9 +169,9 @@ static uint64_t shape_key(int n_c, int n_m, int L) { return (uint64_t(n_c) << 16
 // Enqueue the body of a query: replay (or capture, then replay) the graph of
 // its shape, or launch the kernels directly.
 static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
-  if (!use_graphs()) {
+  if (!use_graphs() || kg->prof) {
     RPQ_CUDA(cudaGetLastError());
-    return launch_query_body(kg->dev, s->d, n_m, L, s->st);
+    return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof);
   }
   const uint64_t key = shape_key(n_c, n_m, L);
   auto it = s->graphs.find(key);
@@ -179,7 +179,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st);
+    const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr);
     const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
     if (rc != RPQ_OK || ce != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -219,12 +219,16 @@ static void fill_stats(const Ctl& c, rpq_stats* st) {
   st->levels_marginal = c.levels[1];
   st->n_cg = int32_t(c.ncg);
   st->n_selected = int32_t(c.nsel);
+  st->work_units = int64_t(c.units);
+  st->work_items = int64_t(c.items);
+  st->frontier_nodes = int64_t(c.frontier);
 }
 
 // Wait for the slot's query and copy its results out.
-static int finish_query(Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
+static int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
   s->busy = false;
   RPQ_CUDA(cudaStreamSynchronize(s->st));
+  if (kg->prof) kg->prof->collect();
   const Ctl& c = *s->h_ctl;
   const int rc = dev_err_to_status(c.err);
   if (rc != RPQ_OK) return rc;
@@ -330,6 +334,7 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
 int rpq_free_kg(rpq_kg* kg) {
   if (!kg) return RPQ_OK;
   for (Slot* s : kg->slots) destroy_slot(s);
+  delete kg->prof;
   cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax);
   cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);
   delete kg;
@@ -363,7 +368,7 @@ int rpq_search(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, 
   if (rc != RPQ_OK) return rc;
   rc = start_query(kg, s, qv);
   if (rc != RPQ_OK) { s->busy = false; cudaStreamSynchronize(s->st); return rc; }
-  return finish_query(s, out, n_out, stats);
+  return finish_query(kg, s, out, n_out, stats);
 }
 
 int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* out, int32_t* n_out,
@@ -382,7 +387,7 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
   auto collect = [&](int si) {
     const int32_t qi = owner[size_t(si)];
     if (qi < 0) return;
-    status[qi] = finish_query(slots[size_t(si)], out + base[size_t(qi)], &n_out[qi], stats ? &stats[qi] : nullptr);
+    status[qi] = finish_query(kg, slots[size_t(si)], out + base[size_t(qi)], &n_out[qi], stats ? &stats[qi] : nullptr);
     if (status[qi] != RPQ_OK) n_out[qi] = 0;
     owner[size_t(si)] = -1;
   };
@@ -449,7 +454,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   auto fail = [&](int code) { cudaFree(d_qlog); return code; };
 #define TC(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error(RPQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return fail(RPQ_ECUDA); } } while (0)
   if (launch_query_setup(d, qv, nullptr, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
-  if (launch_central_part(kg->dev, d, qv.L, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
+  if (launch_central_part(kg->dev, d, qv.L, s->st, nullptr) != RPQ_OK) return fail(RPQ_ECUDA);
   TC(cudaStreamSynchronize(s->st));
   TC(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   TC(cudaMemcpy(H.data(), d.H, n * 8, cudaMemcpyDeviceToHost));
@@ -470,7 +475,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
     tr->n_selected = int32_t(c.nsel);
     for (uint32_t i = 0; i < c.nsel; ++i) tr->selected[i] = c.sel[i];
   }
-  if (launch_marginal_part(kg->dev, d, qv.n_m, qv.L, s->st) != RPQ_OK) return fail(RPQ_ECUDA);
+  if (launch_marginal_part(kg->dev, d, qv.n_m, qv.L, s->st, nullptr) != RPQ_OK) return fail(RPQ_ECUDA);
   TC(cudaStreamSynchronize(s->st));
   TC(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   {
@@ -524,6 +529,36 @@ int rpq_search_device(rpq_kg* kg, const int32_t* d_keywords, int32_t n_c, int32_
   if (rc != RPQ_OK) return rc;
   RPQ_CUDA(cudaMemcpyAsync(d_out, s->d.res, sizeof(rpq_result) * size_t(k), cudaMemcpyDeviceToDevice, s->st));
   RPQ_CUDA(cudaMemcpyAsync(d_n_out, s->d.n_res, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->st));
+  return RPQ_OK;
+}
+
+int rpq_slot_stream(rpq_kg* kg, int32_t slot, void** stream) {
+  if (!kg || !stream || slot < 0 || slot > 255) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
+  Slot* s = nullptr;
+  const int rc = get_slot(kg, size_t(slot), &s);
+  if (rc != RPQ_OK) return rc;
+  *stream = s->st;
+  return RPQ_OK;
+}
+
+int rpq_set_profiling(rpq_kg* kg, int32_t enable) {
+  if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
+  for (Slot* s : kg->slots) cudaStreamSynchronize(s->st);
+  if (enable && !kg->prof) kg->prof = new Prof();
+  if (!enable && kg->prof) { kg->prof->collect(); delete kg->prof; kg->prof = nullptr; }
+  return RPQ_OK;
+}
+
+int rpq_profile_read(rpq_kg* kg, rpq_profile* out, int32_t reset) {
+  if (!kg || !out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  memset(out, 0, sizeof(*out));
+  if (!kg->prof) return RPQ_OK;
+  for (Slot* s : kg->slots) cudaStreamSynchronize(s->st);
+  kg->prof->collect();
+  for (int i = 0; i < RPQ_PROF_CLASSES; ++i) { out->ms[i] = kg->prof->ms[i]; out->launches[i] = kg->prof->launches[i]; }
+  if (reset) {
+    for (int i = 0; i < RPQ_PROF_CLASSES; ++i) { kg->prof->ms[i] = 0; kg->prof->launches[i] = 0; }
+  }
   return RPQ_OK;
 }
 

@@ -26,6 +26,32 @@ int alloc_device(void** p, size_t bytes, int64_t* counter);
 
 struct Slot;
 
+// Optional per-launch timing with CUDA events (profiling mode, no graphs).
+struct Prof {
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<cudaEvent_t> pool;
+  std::vector<Rec> pending;
+  double ms[RPQ_PROF_CLASSES] = {};
+  int64_t launches[RPQ_PROF_CLASSES] = {};
+  cudaEvent_t take() {
+    if (pool.empty()) { cudaEvent_t e; cudaEventCreate(&e); return e; }
+    cudaEvent_t e = pool.back(); pool.pop_back(); return e;
+  }
+  void begin(cudaStream_t st, cudaEvent_t* a) { *a = take(); cudaEventRecord(*a, st); }
+  void end(int cls, cudaStream_t st, cudaEvent_t a) {
+    cudaEvent_t b = take(); cudaEventRecord(b, st); pending.push_back({cls, a, b});
+  }
+  void collect() {  // after the stream has been synchronised
+    for (const Rec& r : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.cls] += t; launches[r.cls] += 1; }
+      pool.push_back(r.a); pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~Prof() { for (cudaEvent_t e : pool) cudaEventDestroy(e); }
+};
+
 }  // namespace rpq
 
 // Opaque graph handle of the C ABI.
@@ -42,6 +68,7 @@ struct rpq_kg {
   int64_t device_bytes = 0;
   std::vector<int64_t> kw_ptr;   // host copy of the postings offsets
   std::vector<rpq::Slot*> slots; // search slots, created on first use
+  rpq::Prof* prof = nullptr;      // profiling mode when non-NULL
 };
 
 namespace rpq {

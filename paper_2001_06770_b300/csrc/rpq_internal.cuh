@@ -90,6 +90,7 @@ struct Ctl {
   uint32_t topk_n[2];          // element counts of the top-k pass buffers
   unsigned long long e_act[2];  // per run
   unsigned long long hits[2];
+  unsigned long long units, items, frontier;  // work totals of both runs
   int32_t levels[2];           // last identified level per run
   int32_t sel[kMaxK];
   uint8_t sel_sc[kMaxK];

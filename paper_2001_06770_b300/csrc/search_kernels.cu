@@ -308,6 +308,8 @@ k_expand(DevKG g, DevSlot s, int run, int l) {
   const bool stop = (nq == 0) || term || (l >= q.L);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->level = uint32_t(l);
+    c->frontier += nq;
+    if (!stop) { c->units += n_work; c->items += n_items; }
     if (stop) {
       c->done = 1;
       c->levels[run] = (nq == 0 && l > 0) ? l - 1 : l;
@@ -618,49 +620,69 @@ __global__ void k_results(DevSlot s) {
 // ------------------------------------------------------------ launchers
 constexpr int kTopkPasses = 4;
 
+// Launch wrapper: brackets the launch with CUDA events in profiling mode.
+template <typename F>
+static void timed(Prof* prof, int cls, cudaStream_t st, F&& launch) {
+  if (!prof) { launch(); return; }
+  cudaEvent_t a;
+  prof->begin(st, &a);
+  launch();
+  prof->end(cls, st, a);
+}
+
 int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st) {
   k_set_query<<<1, 32, 0, st>>>(s, qv, d_kw);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
-// Launch one run (seed + L+1 levels).  nt = number of columns of the run.
-static void launch_run(const DevKG& g, const DevSlot& s, int run, int L, cudaStream_t st) {
+// One run: reset, seed, then L+1 levels of enqueue + expand.
+static void launch_run(const DevKG& g, const DevSlot& s, int run, int L, cudaStream_t st, Prof* prof) {
   const size_t nwords = (size_t(g.n) + 31) / 32;
-  k_run_start<<<1, 32, 0, st>>>(s, run);
-  cudaMemsetAsync(s.vis, 0, ((size_t(g.n) + 3) / 4) * 4, st);
-  cudaMemsetAsync(s.F[0], 0, nwords * 4, st);
-  cudaMemsetAsync(s.F[1], 0, nwords * 4, st);
-  cudaMemsetAsync(s.cf, 0, nwords * 4, st);
   const int sms = num_sms();
-  k_seed<<<sms * 2, 256, 0, st>>>(g, s, run);
+  timed(prof, RPQ_PROF_SETUP, st, [&] {
+    k_run_start<<<1, 32, 0, st>>>(s, run);
+    cudaMemsetAsync(s.vis, 0, ((size_t(g.n) + 3) / 4) * 4, st);
+    cudaMemsetAsync(s.F[0], 0, nwords * 4, st);
+    cudaMemsetAsync(s.F[1], 0, nwords * 4, st);
+    cudaMemsetAsync(s.cf, 0, nwords * 4, st);
+    k_seed<<<sms * 2, 256, 0, st>>>(g, s, run);
+  });
   const int enq_blocks = int(std::min<size_t>(size_t(sms) * 8, (nwords + 31) / 32 + 1));
   for (int l = 0; l <= L; ++l) {
-    k_enqueue<<<enq_blocks, kEnqThreads, 0, st>>>(g, s, run, l);
-    k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, l);
+    timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_blocks, kEnqThreads, 0, st>>>(g, s, run, l); });
+    timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, l); });
   }
 }
 
-int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st) {
-  launch_run(g, s, 0, L, st);
+int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof) {
+  launch_run(g, s, 0, L, st, prof);
   const int sms = num_sms();
-  for (int p = 0; p < kTopkPasses; ++p) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, p);
-  k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+  timed(prof, RPQ_PROF_TOPK, st, [&] {
+    for (int p = 0; p < kTopkPasses; ++p) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, p);
+    k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+  });
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
-int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st) {
+int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
   if (n_m > 0) {
-    k_recover<<<1, kRecThreads, 0, st>>>(g, s);
-    launch_run(g, s, 1, L, st);
+    timed(prof, RPQ_PROF_RECOVER, st, [&] { k_recover<<<1, kRecThreads, 0, st>>>(g, s); });
+    launch_run(g, s, 1, L, st, prof);
   }
-  k_results<<<1, kMaxK, 0, st>>>(s);
+  timed(prof, RPQ_PROF_RESULTS, st, [&] { k_results<<<1, kMaxK, 0, st>>>(s); });
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st) {
-  const int rc = launch_central_part(g, s, L, st);
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
+  const int rc = launch_central_part(g, s, L, st, prof);
   if (rc != RPQ_OK) return rc;
-  return launch_marginal_part(g, s, n_m, L, st);
+  return launch_marginal_part(g, s, n_m, L, st, prof);
+}
+
+// Number of kernels one query launches (for launch accounting).
+int kernels_per_query(int n_m, int L) {
+  const int run = 2 + 2 * (L + 1);            // k_run_start, k_seed, levels
+  return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 1 + run : 0) + 1;
 }
 
 }  // namespace rpq
