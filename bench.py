@@ -316,10 +316,29 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rpq", choices=["rpq", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--profile-only", type=int, default=0, metavar="Q",
+                    help="load the workload, run its first Q queries once through rpq_search and exit "
+                         "(a short command for ncu captures); prints no JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_only:
+        return profile_only(args.profile_only)
     return run(args)
+
+
+def profile_only(nq: int) -> int:
+    import torch
+    import paper_2001_06770_b300 as rpq
+    import rpqgen
+    ds = rpqgen.make_dataset("medium")
+    qs = rpqgen.workload_queries("medium", ds)[:nq]
+    kg = rpq.KG.from_dataset(ds)
+    for q in qs:
+        kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    torch.cuda.synchronize()
+    kg.close()
+    return 0
 
 
 if __name__ == "__main__":
