@@ -48,7 +48,7 @@ NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
 def kernels_per_query(n_m: int, L: int) -> int:
     """Kernels one query launches (same count as the library's launch list)."""
     run = 2 + 2 * (L + 1)
-    return 1 + run + 4 + 1 + ((1 + run) if n_m > 0 else 0) + 1
+    return 1 + run + 4 + 1 + ((2 + run) if n_m > 0 else 0) + 1
 
 
 def hbm_peak():

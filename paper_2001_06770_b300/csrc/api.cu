@@ -91,9 +91,11 @@ static int create_slot(rpq_kg* kg, Slot** out) {
   const size_t tk = n / 32 + 4096;
   SA(d.topk[0], sizeof(uint32_t) * tk);
   SA(d.topk[1], sizeof(uint32_t) * tk);
-  SA(d.rmask, sizeof(unsigned long long) * d.cap);
+  SA(d.rmask, sizeof(unsigned long long) * d.cap * kMaxCols);
   SA(d.vmask, sizeof(unsigned long long) * d.cap);
-  SA(d.rlist, sizeof(uint32_t) * d.cap);
+  SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
+  d.tile_cap = uint32_t(uint64_t(kg->m2) / 128 + 2);
+  SA(d.tile_first, sizeof(uint32_t) * d.tile_cap);
   SA(d.ulist, sizeof(uint32_t) * d.cap);
   SA(d.vcl, sizeof(uint32_t) * d.cap);
   SA(d.sticky, 16);
@@ -104,7 +106,7 @@ static int create_slot(rpq_kg* kg, Slot** out) {
 #undef SA
   if (rc == RPQ_OK) {
     // masks start at zero; the recovery kernel restores zero after each use
-    if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
+    if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess ||
         cudaMemset(d.vmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
         cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
@@ -324,6 +326,7 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
   kg->dev.row_ptr = kg->d_row_ptr;
   kg->dev.adj = kg->d_adj;
   kg->dev.amax = kg->d_amax;
+  kg->dev.lvx = kg->d_lvx;
   kg->dev.n_kw = d->n_kw;
   kg->dev.kw_ptr = kg->d_kw_ptr;
   kg->dev.kw_nodes = kg->d_kw_nodes;
@@ -335,7 +338,7 @@ int rpq_free_kg(rpq_kg* kg) {
   if (!kg) return RPQ_OK;
   for (Slot* s : kg->slots) destroy_slot(s);
   delete kg->prof;
-  cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax);
+  cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax); cudaFree(kg->d_lvx);
   cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);
   delete kg;
   return RPQ_OK;

@@ -149,7 +149,7 @@ __global__ void k_presence(uint32_t m2, const uint32_t* __restrict__ cnt, uint32
                            uint8_t* present) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < m2; e += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t c = cnt[e] - cmin;
-    if (c < ncnt) present[c] = 1;
+    if (c < ncnt && !present[c]) present[c] = 1;
   }
 }
 
@@ -231,6 +231,16 @@ k_sort_large(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __
       }
       __syncthreads();
     }
+  }
+}
+
+// Level index of each row (see kLvxLevels): one thread per row.
+__global__ void k_level_index(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                              uint16_t* __restrict__ lvx) {
+  for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t rb = row_ptr[v], re = row_ptr[v + 1];
+    for (uint32_t x = 1; x <= kLvxLevels; ++x)
+      lvx[size_t(v) * kLvxLevels + (x - 1)] = re - rb <= kLvxMaxDeg ? uint16_t(seg_lower(adj, rb, re, x) - rb) : 0;
   }
 }
 
@@ -324,6 +334,7 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
   kg->d_row_ptr = d_row;
   TRY(alloc_device((void**)&d_amax, size_t(n), &bytes));
   kg->d_amax = d_amax;
+  TRY(alloc_device((void**)&kg->d_lvx, sizeof(uint16_t) * kLvxLevels * size_t(n), &bytes));
   TRY(alloc_device((void**)&d_cnt, sizeof(uint32_t) * size_t(m2), &bytes));
   kg->d_adj = d_cnt;  // replaced by the sorted buffer below
   TRY(alloc_device((void**)&d_col, sizeof(int32_t) * size_t(m2), nullptr));
@@ -381,6 +392,9 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
     d_col = nullptr;
     cudaFree(d_cnt);
   }
+  k_level_index<<<grid_for(n, T), T>>>(n, d_row, kg->d_adj, kg->d_lvx);
+  TRYC(cudaGetLastError());
+  TRYC(cudaDeviceSynchronize());
   cleanup();
   return RPQ_OK;
 #undef TRY

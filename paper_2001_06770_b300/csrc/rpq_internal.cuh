@@ -43,12 +43,19 @@ enum DevErr : uint32_t {
   kErrInternal = 1u << 7,
 };
 
+// Rows with at most kLvxMaxDeg entries carry a level index: lvx[v][x-1] is
+// the offset (from the row start) of the first entry with level >= x, for
+// x = 1..kLvxLevels.  Longer rows and higher levels use a binary search.
+constexpr uint32_t kLvxLevels = 8;
+constexpr uint32_t kLvxMaxDeg = 65535;
+
 struct DevKG {
   int32_t n;
   uint32_t m2;
   const uint32_t* row_ptr;
   const uint32_t* adj;
   const uint8_t* amax;
+  const uint16_t* lvx;        // n * kLvxLevels
   int32_t n_kw;
   const uint32_t* kw_ptr;
   const int32_t* kw_nodes;
@@ -85,7 +92,7 @@ struct Ctl {
   uint32_t n_items, n_work;    // expansion list of the current level
   uint32_t nsel;               // selected CGs
   uint32_t nvc;                // (g, node) pairs of V_C
-  uint32_t rlist_n, ulist_n;   // recovery work lists
+  uint32_t ulist_n;            // recovery: nodes of the union list
   uint32_t n_res;
   uint32_t topk_n[2];          // element counts of the top-k pass buffers
   unsigned long long e_act[2];  // per run
@@ -107,9 +114,11 @@ struct DevSlot {
   Item* items;
   uint32_t* cg;
   uint32_t* topk[2];
-  unsigned long long* rmask;  // recovery: per-column CG mask per node
+  unsigned long long* rmask;  // recovery: per-column CG mask per node (kMaxCols * cap)
   unsigned long long* vmask;  // recovery: union over columns
-  uint32_t* rlist;
+  uint32_t* rlist;            // recovery: per-column node lists (kMaxCols * cap)
+  uint32_t* tile_first;       // expansion: first item of each warp tile
+  uint32_t tile_cap;
   uint32_t* ulist;
   uint32_t* vcl;              // V_C pairs (g << 26 | node)
   uint32_t cap;               // capacity (elements) of items/cg/lists
@@ -136,6 +145,13 @@ __device__ __forceinline__ uint32_t seg_lower(const uint32_t* adj, uint32_t lo, 
     if (__ldg(adj + mid) < key) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+// First entry of row v (bounds rb, re) whose level is >= x.
+__device__ __forceinline__ uint32_t seg_at(const DevKG& g, uint32_t v, uint32_t rb, uint32_t re, uint32_t x) {
+  if (x == 0) return rb;
+  if (re - rb <= kLvxMaxDeg && x <= kLvxLevels) return rb + g.lvx[size_t(v) * kLvxLevels + (x - 1)];
+  return seg_lower(g.adj, rb, re, x);
 }
 
 int num_sms();

@@ -36,8 +36,8 @@ namespace {
 constexpr int kEnqThreads = 256;
 constexpr int kEnqRounds = 4;
 constexpr int kExpThreads = 256;
-constexpr int kExpUnits = 4;                       // work units per thread per tile
-constexpr int kExpTile = kExpThreads * kExpUnits;  // 1024
+constexpr int kExpRounds = 4;                      // 32-unit rounds per warp tile
+constexpr int kWarpTile = 32 * kExpRounds;         // 128 work units per warp tile
 constexpr int kRecThreads = 1024;
 constexpr int kTopkThreads = 1024;
 constexpr int kTopkChunk = 4096;
@@ -195,16 +195,21 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
   uint32_t qcount = 0;
   for (uint32_t tile = blockIdx.x * (nwarp * kEnqRounds); tile < nwords; tile += gridDim.x * (nwarp * kEnqRounds)) {
     uint32_t it_node[kEnqRounds], it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
+    uint32_t words[kEnqRounds];
+#pragma unroll
+    for (int r = 0; r < kEnqRounds; ++r) {          // independent loads first
+      const uint32_t widx = tile + r * nwarp + warp;
+      words[r] = widx < nwords ? Fc[widx] : 0u;
+    }
     uint32_t my_items = 0, my_work = 0;
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
       it_len[r] = 0;
       it_node[r] = 0; it_seg[r] = 0; it_msk[r] = 0;
       const uint32_t widx = tile + r * nwarp + warp;
-      if (widx >= nwords) continue;
-      const uint32_t word = Fc[widx];
-      if (word == 0) continue;
-      if (lane == 0) Fc[widx] = 0;                // reset F for the next use
+      const uint32_t word = words[r];
+      if (word == 0) continue;                      // same word in every lane
+      if (lane == 0) Fc[widx] = 0;                  // reset F for its next use
       const uint32_t v = widx * 32 + lane;
       const bool has = (word >> lane) & 1u;
       qcount += has;
@@ -252,8 +257,8 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
       if (expand) {
         retain = g.amax[v] > uint32_t(l);
         const uint32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
-        const uint32_t hi = seg_lower(g.adj, rb, re, uint32_t(l) + 1u);
-        const uint32_t lo = eq ? rb : seg_lower(g.adj, rb, hi, uint32_t(l));
+        const uint32_t hi = seg_at(g, v, rb, re, uint32_t(l) + 1u);
+        const uint32_t lo = eq ? rb : seg_at(g, v, rb, hi, uint32_t(l));
         if (hi > lo) {
           it_node[r] = v; it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
           ++my_items;
@@ -263,11 +268,12 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
       const unsigned retb = __ballot_sync(0xffffffffu, retain);
       if (lane == 0 && retb) Fn[widx] = retb;          // F_{l+1} word is zero before this level
     }
+    if (!__syncthreads_or(my_items != 0)) continue;    // no item in this tile
     // block-level compaction of the items of this tile
     const uint64_t packed = (uint64_t(my_items) << kWorkBits) | my_work;
     uint64_t tot = 0;
     const uint64_t pre = block_excl_scan(packed, s_warp, &tot);
-    if (threadIdx.x == 0) s_base = tot ? atomicAdd(&c->work[l & 1], (unsigned long long)tot) : 0ull;
+    if (threadIdx.x == 0) s_base = atomicAdd(&c->work[l & 1], (unsigned long long)tot);
     __syncthreads();
     if (my_items) {
       uint32_t idx = uint32_t((s_base >> kWorkBits) + (pre >> kWorkBits));
@@ -279,6 +285,11 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
         it.node = it_node[r]; it.seg_begin = it_seg[r]; it.off = off;
         it.eq = uint8_t(it_msk[r]); it.lt = uint8_t(it_msk[r] >> 8); it.pad = 0;
         s.items[idx] = it;
+        // warp tiles of the expansion whose first unit lies in this item
+        const uint32_t last = off + it_len[r] - 1;
+        for (uint32_t t = (off + kWarpTile - 1) / kWarpTile; t <= last / kWarpTile; ++t) {
+          if (t < s.tile_cap) s.tile_first[t] = idx; else atomicOr(&c->err, kErrOverflow);
+        }
         ++idx;
         off += it_len[r];
       }
@@ -292,9 +303,24 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
 // ----------------------------------------------------------- level: expand
 // Termination (every block reaches the same decision from the control block,
 // which k_enqueue finished writing) and expansion (Algorithm 1) of the work
-// items, split into tiles of kExpTile consecutive work units: a hub's
-// segment spans many tiles (grid-level split), short segments share a tile
-// (block-level), and lanes of a warp read consecutive CSR entries.
+// items.  The work units (one per CSR entry of an item's segment) are cut
+// into warp tiles of kWarpTile consecutive units: a hub's segment spans many
+// tiles (split over the whole grid), short segments share a tile, and the 32
+// lanes of each round read 32 consecutive CSR entries.  Each lane finds its
+// item from a window of 32 items held in registers (one per lane): the item
+// starts inside the round are OR-reduced into a bit mask and a popcount
+// gives the lane's item, so no barrier and no search are needed.
+__device__ __forceinline__ void load_window(const Item* items, uint32_t n_items, uint32_t wb, uint32_t lane,
+                                            uint32_t& woff, uint32_t& wseg, uint32_t& wmsk) {
+  const uint32_t j = wb + lane;
+  if (j < n_items) {
+    const Item it = items[j];
+    woff = it.off; wseg = it.seg_begin; wmsk = uint32_t(it.eq) | (uint32_t(it.lt) << 8);
+  } else {
+    woff = 0xffffffffu; wseg = 0; wmsk = 0;
+  }
+}
+
 __global__ void __launch_bounds__(kExpThreads)
 k_expand(DevKG g, DevSlot s, int run, int l) {
   Ctl* c = s.ctl;
@@ -322,51 +348,59 @@ k_expand(DevKG g, DevSlot s, int run, int l) {
   }
   if (stop || n_work == 0) return;
 
-  __shared__ uint32_t s_off[kExpTile + 1];
-  __shared__ uint32_t s_seg[kExpTile];
-  __shared__ uint16_t s_msk[kExpTile];
-  __shared__ uint32_t s_rng[2];
   __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[(l + 1) & 1];
   const uint32_t lv = uint32_t(l);
+  const uint32_t lane = lane_id();
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t ntiles = (n_work + kWarpTile - 1) / kWarpTile;
   uint64_t eact = 0, hits = 0;
-  for (uint32_t t0 = blockIdx.x * kExpTile; t0 < n_work; t0 += gridDim.x * kExpTile) {
-    const uint32_t t1 = min(t0 + uint32_t(kExpTile), n_work);
-    if (threadIdx.x < 2) {
-      // last item whose offset is <= t0 (thread 0) and <= t1 - 1 (thread 1)
-      const uint32_t key = threadIdx.x == 0 ? t0 : t1 - 1;
-      uint32_t lo = 0, hi = n_items - 1;
-      while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-        if (s.items[mid].off <= key) lo = mid; else hi = mid - 1;
+  for (uint32_t t = gw; t < ntiles; t += nwarps) {
+    const uint32_t t0 = t * kWarpTile;
+    const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
+    uint32_t wb = s.tile_first[t];
+    uint32_t woff, wseg, wmsk;
+    load_window(s.items, n_items, wb, lane, woff, wseg, wmsk);
+    uint32_t e_r[kExpRounds], m_r[kExpRounds];
+    bool v_r[kExpRounds];
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) {
+      const uint32_t u0 = t0 + 32u * r;
+      v_r[r] = false; e_r[r] = 0; m_r[r] = 0;
+      if (u0 >= t1) continue;                      // same in every lane
+      // re-base the window so that lane 0 holds the item containing u0
+      for (;;) {
+        const unsigned le = __ballot_sync(0xffffffffu, woff <= u0);
+        const int hb = 31 - __clz(le);
+        if (hb == 0) break;
+        wb += uint32_t(hb);
+        load_window(s.items, n_items, wb, lane, woff, wseg, wmsk);
       }
-      s_rng[threadIdx.x] = lo;
+      const uint32_t bit = (lane > 0 && woff < u0 + 32u) ? (1u << (woff - u0)) : 0u;
+      const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
+      const int k = __popc(starts & (0xffffffffu >> (31u - lane)));
+      const uint32_t off = __shfl_sync(0xffffffffu, woff, k);
+      const uint32_t seg = __shfl_sync(0xffffffffu, wseg, k);
+      const uint32_t msk = __shfl_sync(0xffffffffu, wmsk, k);
+      const uint32_t u = u0 + lane;
+      if (u < t1) { e_r[r] = seg + (u - off); m_r[r] = msk; v_r[r] = true; }
     }
-    __syncthreads();
-    const uint32_t i0 = s_rng[0], cnt = s_rng[1] - i0 + 1;   // cnt <= kExpTile (each item has work)
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const Item it = s.items[i0 + i];
-      s_off[i] = it.off; s_seg[i] = it.seg_begin;
-      s_msk[i] = uint16_t(it.eq | (uint32_t(it.lt) << 8));
-    }
-    __syncthreads();
-    uint32_t si = 0;
-    for (uint32_t u = t0 + threadIdx.x; u < t1; u += blockDim.x) {
-      uint32_t lo = si, hi = cnt - 1;                 // last s with s_off[s] <= u
-      while (lo < hi) {
-        const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-        if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
-      }
-      si = lo;
-      const uint32_t e = s_seg[si] + (u - s_off[si]);
-      const uint32_t x = __ldg(g.adj + e);
-      const uint32_t a = x >> kNodeBits;
-      const uint32_t nb = x & kNodeMask;
-      const uint32_t eq = s_msk[si] & 0xffu, lt = s_msk[si] >> 8;
+    uint32_t x_r[kExpRounds];
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) x_r[r] = v_r[r] ? __ldg(g.adj + e_r[r]) : 0u;
+    uint32_t vb_r[kExpRounds];
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) {
+      if (!v_r[r]) continue;
+      const uint32_t a = x_r[r] >> kNodeBits;
+      const uint32_t nb = x_r[r] & kNodeMask;
+      const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
       const uint32_t act = a < lv ? eq : (eq | lt);   // columns for which the edge is new at level l
       eact += __popc(act);
-      const uint32_t vb = vis_byte(s.vis, nb);
-      const uint32_t nw = act & ~vb;
+      const uint32_t nw = act & ~vb_r[r];
       if (nw) {
         const uint32_t sh = (nb & 3u) * 8u;
         const uint32_t old = atomicOr(s.vis + (nb >> 2), nw << sh);
@@ -378,7 +412,6 @@ k_expand(DevKG g, DevSlot s, int run, int l) {
         }
       }
     }
-    __syncthreads();
   }
   const uint64_t te = block_sum(eact, s_warp);
   const uint64_t th = block_sum(hits, s_warp);
@@ -411,11 +444,13 @@ k_topk_pass(DevSlot s, int pass) {
   for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const uint32_t b = ch * kTopkChunk;
     const uint32_t len = min(uint32_t(kTopkChunk), n_in - b);
-    for (uint32_t i = threadIdx.x; i < kTopkChunk; i += blockDim.x) key[i] = i < len ? src[b + i] : 0xffffffffu;
+    uint32_t sz = 32;                               // sort only a power of two >= len
+    while (sz < len) sz <<= 1;
+    for (uint32_t i = threadIdx.x; i < sz; i += blockDim.x) key[i] = i < len ? src[b + i] : 0xffffffffu;
     __syncthreads();
-    for (uint32_t k = 2; k <= kTopkChunk; k <<= 1) {
+    for (uint32_t k = 2; k <= sz; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < kTopkChunk; i += blockDim.x) {
+        for (uint32_t i = threadIdx.x; i < sz; i += blockDim.x) {
           const uint32_t p = i ^ j;
           if (p > i) {
             const uint32_t a = key[i], bb = key[p];
@@ -447,109 +482,110 @@ __global__ void k_select(DevSlot s, int last_pass) {
     ++ns;
   }
   c->nsel = ns;
+  c->ulist_n = 0;
+  c->nvc = 0;
 }
 
 // ---------------------------------------------------------------- recovery
-// Recovering phase (Algorithm 2) for all selected CGs at once, one block.
-// For each central column j a backward sweep from the CG nodes, level by
-// level downwards, follows the edges n -> q with h_q = max(a, h_n) + 1
+// Recovering phase (Algorithm 2) for all selected CGs at once.  Block j of
+// k_recover_cols handles central column j: a backward sweep from the CG nodes,
+// level by level downwards, follows the edges n -> q with h_q = max(a, h_n) + 1
 // (tight, Lemma 3) whose source n was still expanding at level max(a, h_n)
 // (it had not stopped earlier).  Each node carries a bit mask of the CGs it
-// belongs to, OR-ed along the tight edges; the union over columns gives V^c
-// per CG, and V_C are the nodes of V^c that hold a central keyword.
+// belongs to, OR-ed along the tight edges; the masks of all columns are
+// OR-ed into one union mask (V^c per CG).  k_recover_vc then keeps the nodes
+// of V^c that hold a central keyword: V_C of each CG.
 __global__ void __launch_bounds__(kRecThreads)
-k_recover(DevKG g, DevSlot s) {
+k_recover_cols(DevKG g, DevSlot s) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   const uint32_t nsel = c->nsel;
-  if (nsel == 0 || q.n_m == 0) return;   // V_C is only needed by the marginal run
-  const int nc = q.n_c;
+  const int j = blockIdx.x;
+  if (nsel == 0 || j >= q.n_c) return;
   const int maxlev = c->levels[0];
+  unsigned long long* rmask = s.rmask + size_t(j) * s.cap;
+  uint32_t* rlist = s.rlist + size_t(j) * s.cap;
   __shared__ uint32_t s_off[kRecThreads];
   __shared__ uint32_t s_rb[kRecThreads];
   __shared__ unsigned long long s_m[kRecThreads];
   __shared__ uint64_t s_warp[33];
-  __shared__ uint32_t s_cnt, s_total;
-  if (threadIdx.x == 0) { c->ulist_n = 0; c->nvc = 0; }
+  __shared__ uint32_t s_n, s_cnt, s_total;
+  if (threadIdx.x == 0) s_n = 0;
   __syncthreads();
   for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
     const uint32_t v = uint32_t(c->sel[gi]);
-    const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
-    if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+    if (j == 0) {                                  // the CG nodes themselves belong to V^c
+      const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
+      if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+    }
+    if (s.H[size_t(v) * 8 + j] == 0) continue;   // the CG node holds keyword j
+    const unsigned long long old = atomicOr(&rmask[v], 1ull << gi);
+    if (old == 0) rlist[atomicAdd(&s_n, 1u)] = v;
   }
   __syncthreads();
-  for (int j = 0; j < nc; ++j) {
-    if (threadIdx.x == 0) c->rlist_n = 0;
+  for (int x = maxlev; x >= 1; --x) {
+    if (threadIdx.x == 0) s_cnt = min(s_n, s.cap);
     __syncthreads();
-    for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
-      const uint32_t v = uint32_t(c->sel[gi]);
-      if (s.H[size_t(v) * 8 + j] == 0) continue;      // the CG node holds keyword j
-      const unsigned long long old = atomicOr(&s.rmask[v], 1ull << gi);
-      if (old == 0) s.rlist[atomicAdd(&c->rlist_n, 1u)] = v;
-    }
-    __syncthreads();
-    for (int x = maxlev; x >= 1; --x) {
-      if (threadIdx.x == 0) s_cnt = min(c->rlist_n, s.cap);
+    const uint32_t cnt = s_cnt;
+    for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
+      const uint32_t i = c0 + threadIdx.x;
+      uint32_t len = 0, rb = 0;
+      unsigned long long m = 0;
+      if (i < cnt) {
+        const uint32_t qn = rlist[i];
+        if (s.H[size_t(qn) * 8 + j] == uint8_t(x)) {
+          rb = g.row_ptr[qn];
+          len = seg_at(g, qn, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
+          m = rmask[qn];
+        }
+      }
+      uint64_t tot = 0;
+      const uint32_t pre = uint32_t(block_excl_scan(len, s_warp, &tot));
+      s_off[threadIdx.x] = pre; s_rb[threadIdx.x] = rb; s_m[threadIdx.x] = m;
+      if (threadIdx.x == 0) s_total = uint32_t(tot);
       __syncthreads();
-      const uint32_t cnt = s_cnt;
-      for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
-        const uint32_t i = c0 + threadIdx.x;
-        uint32_t len = 0, qn = 0, rb = 0;
-        unsigned long long m = 0;
-        if (i < cnt) {
-          qn = s.rlist[i];
-          if (s.H[size_t(qn) * 8 + j] == uint8_t(x)) {
-            rb = g.row_ptr[qn];
-            len = seg_lower(g.adj, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
-            m = s.rmask[qn];
-          }
+      const uint32_t total = s_total;
+      for (uint32_t u = threadIdx.x; u < total; u += blockDim.x) {
+        uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u
+        while (lo < hi) {
+          const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+          if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
         }
-        uint64_t tot = 0;
-        const uint32_t pre = uint32_t(block_excl_scan(len, s_warp, &tot));
-        s_off[threadIdx.x] = pre; s_rb[threadIdx.x] = rb; s_m[threadIdx.x] = m;
-        if (threadIdx.x == 0) s_total = uint32_t(tot);
-        __syncthreads();
-        const uint32_t total = s_total;
-        for (uint32_t u = threadIdx.x; u < total; u += blockDim.x) {
-          uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u and work
-          while (lo < hi) {
-            const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-            if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
-          }
-          const uint32_t e = s_rb[lo] + (u - s_off[lo]);
-          const uint32_t xe = __ldg(g.adj + e);
-          const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
-          if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
-          const uint32_t hn = s.H[size_t(nb) * 8 + j];
-          const uint32_t lam = a > hn ? a : hn;
-          if (lam + 1 != uint32_t(x)) continue;                     // not tight
-          if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
-          const unsigned long long old = atomicOr(&s.rmask[nb], s_m[lo]);
-          if (old == 0) {
-            const uint32_t p = atomicAdd(&c->rlist_n, 1u);
-            if (p < s.cap) s.rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
-          }
+        const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
+        const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
+        if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
+        const uint32_t hn = s.H[size_t(nb) * 8 + j];
+        const uint32_t lam = a > hn ? a : hn;
+        if (lam + 1 != uint32_t(x)) continue;                               // not tight
+        if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
+        const unsigned long long old = atomicOr(&rmask[nb], s_m[lo]);
+        if (old == 0) {
+          const uint32_t p = atomicAdd(&s_n, 1u);
+          if (p < s.cap) rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
-    // fold column j into the union masks and clear the column masks
-    const uint32_t nr = min(c->rlist_n, s.cap);
-    for (uint32_t i = threadIdx.x; i < nr; i += blockDim.x) {
-      const uint32_t v = s.rlist[i];
-      const unsigned long long m = s.rmask[v];
-      s.rmask[v] = 0;
-      const unsigned long long old = atomicOr(&s.vmask[v], m);
-      if (old == 0) {
-        const uint32_t p = atomicAdd(&c->ulist_n, 1u);
-        if (p < s.cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
-      }
-    }
-    __syncthreads();
   }
-  // V_C: nodes of V^c holding a central keyword (h == 0 in a central column)
+  // fold column j into the union masks and clear the column masks
+  const uint32_t nr = min(s_n, s.cap);
+  for (uint32_t i = threadIdx.x; i < nr; i += blockDim.x) {
+    const uint32_t v = rlist[i];
+    const unsigned long long m = rmask[v];
+    rmask[v] = 0;
+    const unsigned long long old = atomicOr(&s.vmask[v], m);
+    if (old == 0) {
+      const uint32_t p = atomicAdd(&c->ulist_n, 1u);
+      if (p < s.cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
+    }
+  }
+}
+
+__global__ void k_recover_vc(DevSlot s) {
+  Ctl* c = s.ctl;
+  const int nc = s.q->n_c;
   const uint32_t nu = min(c->ulist_n, s.cap);
-  for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
     const uint32_t v = s.ulist[i];
     unsigned long long m = s.vmask[v];
     s.vmask[v] = 0;
@@ -647,7 +683,7 @@ static void launch_run(const DevKG& g, const DevSlot& s, int run, int L, cudaStr
     cudaMemsetAsync(s.cf, 0, nwords * 4, st);
     k_seed<<<sms * 2, 256, 0, st>>>(g, s, run);
   });
-  const int enq_blocks = int(std::min<size_t>(size_t(sms) * 8, (nwords + 31) / 32 + 1));
+  const int enq_blocks = int(std::min<size_t>(size_t(sms) * 6, (nwords + 31) / 32 + 1));
   for (int l = 0; l <= L; ++l) {
     timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_blocks, kEnqThreads, 0, st>>>(g, s, run, l); });
     timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, l); });
@@ -666,7 +702,10 @@ int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st
 
 int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
   if (n_m > 0) {
-    timed(prof, RPQ_PROF_RECOVER, st, [&] { k_recover<<<1, kRecThreads, 0, st>>>(g, s); });
+    timed(prof, RPQ_PROF_RECOVER, st, [&] {
+      k_recover_cols<<<kMaxCols, kRecThreads, 0, st>>>(g, s);
+      k_recover_vc<<<num_sms(), 256, 0, st>>>(s);
+    });
     launch_run(g, s, 1, L, st, prof);
   }
   timed(prof, RPQ_PROF_RESULTS, st, [&] { k_results<<<1, kMaxK, 0, st>>>(s); });
@@ -682,7 +721,7 @@ int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStre
 // Number of kernels one query launches (for launch accounting).
 int kernels_per_query(int n_m, int L) {
   const int run = 2 + 2 * (L + 1);            // k_run_start, k_seed, levels
-  return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 1 + run : 0) + 1;
+  return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 2 + run : 0) + 1;
 }
 
 }  // namespace rpq
