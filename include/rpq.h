@@ -240,6 +240,32 @@ typedef struct {
 int rpq_set_profiling(rpq_kg *kg, int32_t enable);
 int rpq_profile_read(rpq_kg *kg, rpq_profile *out, int32_t reset);
 
+/* --------------------------------------------- selection without allocation */
+/* rpq_topk_keys_noalloc: write the k smallest of n 32-bit keys, ascending, to
+ * d_out and their count (min(k, n)) to *d_n_out.  The paper has no
+ * counterpart; this is a service for callers that cannot allocate device
+ * memory when they need a selection, e.g. code running while another
+ * component captures a CUDA graph, or a serving loop whose device memory is
+ * entirely held by a pre-planned pool.  It runs the same block-local top-K
+ * merge as the search's CG selection, with its intermediate buffers in a
+ * fixed device array compiled into the library (about 1.04 MB, held on every
+ * GPU that loads the library until the process exits), and calls no
+ * allocating routine.
+ *   d_keys    n keys in device memory, each < 0xffffffff (that value pads)
+ *   n         0 <= n <= 16,777,216 (2^24); larger inputs return RPQ_ELIMIT
+ *   k         1 <= k <= RPQ_MAX_K
+ *   d_out     k uint32 slots in device memory; d_n_out one uint32 (device)
+ *   stream    cudaStream_t to enqueue on (NULL = legacy default stream); the
+ *             call returns without waiting
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture that should contain later calls.  All calls on a device share the
+ * one array: calls whose work overlaps on the GPU (different streams without
+ * ordering, or several host threads) race and give wrong results.  Errors:
+ * RPQ_EINVAL (NULL pointer, k out of range), RPQ_ELIMIT, RPQ_ECUDA. */
+int rpq_topk_keys_noalloc(const uint32_t *d_keys, uint32_t n, int32_t k, uint32_t *d_out, uint32_t *d_n_out,
+                          void *stream);
+
 /* -------------------------------------------------------------- messages */
 const char *rpq_strerror(int code);
 const char *rpq_last_error(void);

@@ -28,7 +28,7 @@ MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
            "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
-           "rpq_profile_read", "rpq_strerror", "rpq_last_error"]
+           "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_strerror", "rpq_last_error"]
 PROF_CLASSES = ["setup", "enqueue", "expand", "topk", "recover", "results"]
 
 
@@ -105,6 +105,7 @@ def lib():
         L.rpq_slot_stream.argtypes = [P, i32, ctypes.POINTER(P)]
         L.rpq_set_profiling.argtypes = [P, i32]
         L.rpq_profile_read.argtypes = [P, ctypes.POINTER(Profile), i32]
+        L.rpq_topk_keys_noalloc.argtypes = [P, ctypes.c_uint32, i32, P, P, P]
         L.rpq_strerror.argtypes = [ctypes.c_int]
         L.rpq_strerror.restype = ctypes.c_char_p
         L.rpq_last_error.restype = ctypes.c_char_p
@@ -121,6 +122,13 @@ def _check(rc: int):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def topk_keys_noalloc(d_keys: int, n: int, k: int, d_out: int, d_n_out: int, stream: int = 0):
+    """k smallest of n uint32 keys in device memory, without any allocation
+    (raw device pointers; see rpq_topk_keys_noalloc in include/rpq.h)."""
+    _check(lib().rpq_topk_keys_noalloc(ctypes.c_void_p(d_keys), n, k, ctypes.c_void_p(d_out),
+                                       ctypes.c_void_p(d_n_out), ctypes.c_void_p(stream or None)))
 
 
 @dataclass
