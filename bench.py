@@ -45,12 +45,6 @@ FALLBACK_HBM = 6400.0
 NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
 
 
-def kernels_per_query(n_m: int, L: int) -> int:
-    """Kernels one query launches (same count as the library's launch list)."""
-    run = 2 + 2 * (L + 1)
-    return 1 + run + 4 + 1 + ((2 + run) if n_m > 0 else 0) + 1
-
-
 def hbm_peak():
     try:
         pk = json.load(open(PEAKS_FILE))
@@ -208,7 +202,7 @@ def run(args):
         stats.append(st)
         host_res.append(r)
     e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
-    launches_per_step = sum(kernels_per_query(len(q.marginal), q.max_depth) for q in qs)
+    launches_per_step = sum(st["kernels"] for st in stats)
 
     for _ in range(args.warmup):
         step_device()

@@ -141,6 +141,7 @@ typedef struct {
     int64_t work_units;     /* CSR entries read by the expansions (both runs) */
     int64_t work_items;     /* (frontier node, level) expansion items */
     int64_t frontier_nodes; /* sum over levels of |Q_l| (both runs) */
+    int64_t kernels;        /* kernels the query launches when replayed from its CUDA graph */
 } rpq_stats;
 
 /* Search one query (Sections 3-4): central run -> top-w CGs -> recovery of

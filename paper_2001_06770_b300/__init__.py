@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("hits_central", ctypes.c_int64), ("hits_marginal", ctypes.c_int64),
                 ("levels_central", ctypes.c_int32), ("levels_marginal", ctypes.c_int32),
                 ("n_cg", ctypes.c_int32), ("n_selected", ctypes.c_int32),
-                ("work_units", ctypes.c_int64), ("work_items", ctypes.c_int64), ("frontier_nodes", ctypes.c_int64)]
+                ("work_units", ctypes.c_int64), ("work_items", ctypes.c_int64), ("frontier_nodes", ctypes.c_int64),
+                ("kernels", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -14,6 +14,12 @@ namespace rpq {
 
 int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
 int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
+void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof);
+void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
+                  cudaGraphConditionalHandle loop, bool in_graph);
+void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof);
+void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof);
+int kernels_fixed_per_query(int n_m);
 int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof);
 int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
 
@@ -48,6 +54,7 @@ struct Slot {
   std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
   bool busy = false;
   int32_t pending_k = 0;
+  int32_t pending_nm = 0;
 };
 
 static bool use_graphs() {
@@ -80,7 +87,8 @@ static int create_slot(rpq_kg* kg, Slot** out) {
   };
   int rc = RPQ_OK;
 #define SA(ptr, bytes) do { if (rc == RPQ_OK) rc = A((void**)&(ptr), (bytes)); } while (0)
-  SA(d.H, n * 8 + 16);
+  d.hp = uint32_t((n + 15) / 16 * 16);
+  SA(d.H, size_t(d.hp) * kMaxCols + 16);
   SA(d.vis, ((n + 3) / 4) * 4 + 16);
   SA(d.F[0], nwords * 4 + 16);
   SA(d.F[1], nwords * 4 + 16);
@@ -96,6 +104,9 @@ static int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
   d.tile_cap = uint32_t(uint64_t(kg->m2) / 128 + 2);
   SA(d.tile_first, sizeof(uint32_t) * d.tile_cap);
+  d.fq_limit = uint32_t(std::min<size_t>(d.cap, std::max<size_t>(nwords, 4096)));
+  SA(d.fq[0], sizeof(uint32_t) * d.fq_limit);
+  SA(d.fq[1], sizeof(uint32_t) * d.fq_limit);
   SA(d.ulist, sizeof(uint32_t) * d.cap);
   SA(d.vcl, sizeof(uint32_t) * d.cap);
   SA(d.sticky, 16);
@@ -166,32 +177,85 @@ static int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool*
   return RPQ_OK;
 }
 
-static uint64_t shape_key(int n_c, int n_m, int L) { return (uint64_t(n_c) << 16) | (uint64_t(n_m) << 8) | uint64_t(L); }
+// Graph of one query shape: captured segments as child graphs, and the level
+// loop of each run as a WHILE conditional node whose body (k_enqueue,
+// k_expand) repeats until k_expand ends it.
+static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, cudaGraphExec_t* out) {
+  cudaGraph_t main = nullptr;
+  RPQ_CUDA(cudaGraphCreate(&main, 0));
+  cudaGraphNode_t prev = nullptr;
+  int rc = RPQ_OK;
+  auto fail = [&](const char* what, cudaError_t e) {
+    cudaGetLastError();
+    set_error(RPQ_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
+    rc = RPQ_ECUDA;
+  };
+  auto add_segment = [&](auto&& launch) {
+    if (rc != RPQ_OK) return;
+    cudaGraph_t child = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { fail("begin capture", e); return; }
+    launch();
+    e = cudaStreamEndCapture(s->st, &child);
+    if (e != cudaSuccess) { if (child) cudaGraphDestroy(child); fail("end capture", e); return; }
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddChildGraphNode(&node, main, prev ? &prev : nullptr, prev ? 1 : 0, child);
+    cudaGraphDestroy(child);
+    if (e != cudaSuccess) { fail("child node", e); return; }
+    prev = node;
+  };
+  auto add_loop = [&](int run) {
+    if (rc != RPQ_OK) return;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { fail("conditional handle", e); return; }
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, main, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp);
+    if (e != cudaSuccess) { fail("conditional node", e); return; }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { fail("capture loop body", e); return; }
+    launch_level(kg->dev, s->d, run, s->st, nullptr, h, true);
+    cudaGraph_t got = nullptr;
+    e = cudaStreamEndCapture(s->st, &got);
+    if (e != cudaSuccess) { fail("end loop body", e); return; }
+    prev = node;
+  };
+  add_segment([&] { launch_run_setup(kg->dev, s->d, 0, s->st, nullptr); });
+  add_loop(0);
+  add_segment([&] {
+    launch_select_recover(kg->dev, s->d, n_m, s->st, nullptr);
+    if (n_m > 0) launch_run_setup(kg->dev, s->d, 1, s->st, nullptr);
+  });
+  if (n_m > 0) add_loop(1);
+  add_segment([&] { launch_results(s->d, s->st, nullptr); });
+  if (rc == RPQ_OK) {
+    const cudaError_t e = cudaGraphInstantiate(out, main, 0);
+    if (e != cudaSuccess) fail("instantiate", e);
+  }
+  cudaGraphDestroy(main);
+  return rc;
+}
 
-// Enqueue the body of a query: replay (or capture, then replay) the graph of
+// Enqueue the body of a query: replay (or build, then replay) the graph of
 // its shape, or launch the kernels directly.
 static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
   if (!use_graphs() || kg->prof) {
     RPQ_CUDA(cudaGetLastError());
     return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof);
   }
-  const uint64_t key = shape_key(n_c, n_m, L);
+  (void)n_c;
+  (void)L;   // the graph's loops run as many levels as the query needs
+  const uint64_t key = uint64_t(n_m > 0 ? 1 : 0);
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
-    cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr);
-    const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
-    if (rc != RPQ_OK || ce != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      set_error(RPQ_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-      return RPQ_ECUDA;
-    }
-    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) { set_error(RPQ_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie)); return RPQ_ECUDA; }
+    const int rc = build_query_graph(kg, s, n_m, &exec);
+    if (rc != RPQ_OK) return rc;
     it = s->graphs.emplace(key, exec).first;
   }
   RPQ_CUDA(cudaGraphLaunch(it->second, s->st));
@@ -208,6 +272,7 @@ static int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
   RPQ_CUDA(cudaMemcpyAsync(s->h_res, s->d.res, sizeof(rpq_result) * size_t(qv.k), cudaMemcpyDeviceToHost, s->st));
   s->busy = true;
   s->pending_k = qv.k;
+  s->pending_nm = qv.n_m;
   return RPQ_OK;
 }
 
@@ -238,6 +303,7 @@ static int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rp
   if (out && nr) memcpy(out, s->h_res, sizeof(rpq_result) * size_t(nr));
   if (n_out) *n_out = nr;
   fill_stats(c, stats);
+  if (stats) stats->kernels = kernels_fixed_per_query(s->pending_nm) + 2 * int64_t(c.iters[0] + c.iters[1]);
   return RPQ_OK;
 }
 
@@ -429,7 +495,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   DevSlot d = s->d;
   d.qlog = d_qlog;
   d.qcap = uint32_t(qcap);
-  std::vector<uint8_t> H(n * 8), vis(((n + 3) / 4) * 4);
+  std::vector<uint8_t> H(size_t(s->d.hp) * kMaxCols), vis(((n + 3) / 4) * 4);
   std::vector<uint32_t> qlog;
   Ctl c{};
   auto frontiers = [&](uint32_t from, uint32_t to, int64_t* ptr, int32_t* dst, int64_t cap, int32_t* levels) {
@@ -452,7 +518,8 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   auto hmat = [&](uint8_t* dst, int nt) {
     if (!dst) return;
     for (size_t v = 0; v < n; ++v)
-      for (int j = 0; j < nt; ++j) dst[v * size_t(nt) + size_t(j)] = ((vis[v] >> j) & 1) ? H[v * 8 + size_t(j)] : kInf;
+      for (int j = 0; j < nt; ++j)
+        dst[v * size_t(nt) + size_t(j)] = ((vis[v] >> j) & 1) ? H[size_t(j) * d.hp + v] : kInf;
   };
   auto fail = [&](int code) { cudaFree(d_qlog); return code; };
 #define TC(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error(RPQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return fail(RPQ_ECUDA); } } while (0)
@@ -460,7 +527,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   if (launch_central_part(kg->dev, d, qv.L, s->st, nullptr) != RPQ_OK) return fail(RPQ_ECUDA);
   TC(cudaStreamSynchronize(s->st));
   TC(cudaMemcpy(&c, d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  TC(cudaMemcpy(H.data(), d.H, n * 8, cudaMemcpyDeviceToHost));
+  TC(cudaMemcpy(H.data(), d.H, H.size(), cudaMemcpyDeviceToHost));
   TC(cudaMemcpy(vis.data(), d.vis, n, cudaMemcpyDeviceToHost));
   const uint32_t nqc = std::min<uint32_t>(c.qlog_n, uint32_t(qcap));
   qlog.resize(nqc);
@@ -490,7 +557,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
     if (tr->vc) for (size_t i = 0; i < vc.size() && int64_t(i) < tr->vc_cap; ++i) tr->vc[i] = vc[i];
   }
   if (qv.n_m > 0 && c.levels[1] >= 0) {
-    TC(cudaMemcpy(H.data(), d.H, n * 8, cudaMemcpyDeviceToHost));
+    TC(cudaMemcpy(H.data(), d.H, H.size(), cudaMemcpyDeviceToHost));
     TC(cudaMemcpy(vis.data(), d.vis, n, cudaMemcpyDeviceToHost));
     hmat(tr->h_marginal, qv.n_m);
     const uint32_t nqa = std::min<uint32_t>(c.qlog_n, uint32_t(qcap));

@@ -240,7 +240,7 @@ __global__ void k_level_index(int32_t n, const uint32_t* __restrict__ row_ptr, c
   for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t rb = row_ptr[v], re = row_ptr[v + 1];
     for (uint32_t x = 1; x <= kLvxLevels; ++x)
-      lvx[size_t(v) * kLvxLevels + (x - 1)] = re - rb <= kLvxMaxDeg ? uint16_t(seg_lower(adj, rb, re, x) - rb) : 0;
+      lvx[size_t(x - 1) * size_t(n) + size_t(v)] = re - rb <= kLvxMaxDeg ? uint16_t(seg_lower(adj, rb, re, x) - rb) : 0;
   }
 }
 

@@ -8,8 +8,8 @@
 //   kw_ptr   uint32[n_kw+1], kw_nodes int32[]   keyword postings (V_t)
 //
 // Per-search state (one "slot"; several slots run concurrently):
-//   H        uint8[n][8]   Node-Keyword Matrix (Section 4.2.1), hit levels,
-//                          valid only where the visited bit is set
+//   H        uint8[8][hp]  Node-Keyword Matrix (Section 4.2.1), column-major
+//                          hit levels, valid only where the visited bit is set
 //   vis      uint8[n]      visited bits, bit j = column j reached (read as
 //                          bytes, updated with 32-bit atomicOr)
 //   F[2]     uint32[n/32]  Frontier Flag Array, double buffered by level
@@ -43,7 +43,7 @@ enum DevErr : uint32_t {
   kErrInternal = 1u << 7,
 };
 
-// Rows with at most kLvxMaxDeg entries carry a level index: lvx[v][x-1] is
+// Rows with at most kLvxMaxDeg entries carry a level index: lvx[x-1][v] is
 // the offset (from the row start) of the first entry with level >= x, for
 // x = 1..kLvxLevels.  Longer rows and higher levels use a binary search.
 constexpr uint32_t kLvxLevels = 8;
@@ -55,7 +55,7 @@ struct DevKG {
   const uint32_t* row_ptr;
   const uint32_t* adj;
   const uint8_t* amax;
-  const uint16_t* lvx;        // n * kLvxLevels
+  const uint16_t* lvx;        // kLvxLevels * n, level-major
   int32_t n_kw;
   const uint32_t* kw_ptr;
   const int32_t* kw_nodes;
@@ -93,6 +93,10 @@ struct Ctl {
   uint32_t nsel;               // selected CGs
   uint32_t nvc;                // (g, node) pairs of V_C
   uint32_t ulist_n;            // recovery: nodes of the union list
+  uint32_t lvl_enq, lvl_exp;   // Glevel of the next k_enqueue / the current k_expand
+  uint32_t fq_n[2];            // frontier queue lengths per level parity
+  uint32_t fq_over[2];         // queue abandoned (frontier too large): use the bitmap
+  uint32_t iters[2];           // level kernel pairs executed per run
   uint32_t n_res;
   uint32_t topk_n[2];          // element counts of the top-k pass buffers
   unsigned long long e_act[2];  // per run
@@ -119,6 +123,9 @@ struct DevSlot {
   uint32_t* rlist;            // recovery: per-column node lists (kMaxCols * cap)
   uint32_t* tile_first;       // expansion: first item of each warp tile
   uint32_t tile_cap;
+  uint32_t* fq[2];            // frontier queues (nodes of F), per level parity
+  uint32_t fq_limit;          // queue used while it holds at most this many nodes
+  uint32_t hp;                // column pitch of H (H[j * hp + v])
   uint32_t* ulist;
   uint32_t* vcl;              // V_C pairs (g << 26 | node)
   uint32_t cap;               // capacity (elements) of items/cg/lists
@@ -150,7 +157,7 @@ __device__ __forceinline__ uint32_t seg_lower(const uint32_t* adj, uint32_t lo, 
 // First entry of row v (bounds rb, re) whose level is >= x.
 __device__ __forceinline__ uint32_t seg_at(const DevKG& g, uint32_t v, uint32_t rb, uint32_t re, uint32_t x) {
   if (x == 0) return rb;
-  if (re - rb <= kLvxMaxDeg && x <= kLvxLevels) return rb + g.lvx[size_t(v) * kLvxLevels + (x - 1)];
+  if (re - rb <= kLvxMaxDeg && x <= kLvxLevels) return rb + g.lvx[size_t(x - 1) * size_t(g.n) + v];
   return seg_lower(g.adj, rb, re, x);
 }
 

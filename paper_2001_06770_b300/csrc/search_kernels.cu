@@ -1,20 +1,22 @@
 // Search kernels of one radial-pattern query (Section 4).
 //
-// One query runs as a fixed sequence of launches on the slot's stream:
+// One query runs as a sequence of launches on the slot's stream:
 //   k_set_query                       copy parameters, reset the control block
 //   per run (central, then marginal):
-//     memsets of vis / F / cf, k_seed (Section 4.2.1 initialisation)
-//     for l = 0..L:  k_enqueue(l)     frontier enqueue + reset (4.2.2) and
+//     k_run_start, memsets of vis / F / cf, k_seed (Section 4.2.1)
+//     per Glevel l:  k_enqueue        frontier enqueue + reset (4.2.2) and
 //                                     result identification (4.2.3,
 //                                     Theorem 3; PTC stop; RPG match)
-//                    k_expand(l)      termination decision + expansion
+//                    k_expand         termination decision + expansion
 //                                     (Algorithm 1) of the newly active edges
 //   after the central run: k_topk_pass x4, k_select (top-w CGs),
-//                          k_recover (Algorithm 2 -> V_C of each CG)
+//                          k_recover_cols, k_recover_vc (Algorithm 2 -> V_C)
 //   at the end:            k_results (Eq. 6, top-k by (S^r, id))
-// Every kernel first reads the control block and returns at once when the
-// current run has already finished, so the sequence can be captured once per
-// query shape (|C|, |M|, L) as a CUDA graph and replayed.
+// The Glevel is kept in the control block, so the two level kernels form the
+// body of a CUDA-graph WHILE node that k_expand ends when the run stops; the
+// graph of each query shape (|C|, |M|, L) is built once and replayed.  Without
+// a graph (profiling, tracing) the host launches L+1 level pairs and the
+// kernels of finished runs return at once.
 //
 // Exactness: the expansion at level l touches, for frontier node v and
 // column j, only the edges with max(h[v][j], a) == l (the rows are sorted by
@@ -108,13 +110,36 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->done = (run == 1 && (s.q->n_m == 0 || c->nsel == 0)) ? 1u : 0u;
   c->work[0] = c->work[1] = 0;
   c->nq[0] = c->nq[1] = 0;
+  c->fq_n[0] = c->fq_n[1] = 0;
+  c->fq_over[0] = c->fq_over[1] = 0;
+  c->lvl_enq = c->lvl_exp = 0;
   c->level = 0;
   c->last_expanded = -1;
 }
 
+// Append the flagged lanes' nodes to frontier queue p (warp aggregated).  The
+// queue is abandoned (flag set) once it would exceed its limit; the bitmap F
+// stays complete either way.
+__device__ __forceinline__ void queue_push(const DevSlot& s, Ctl* c, int p, bool flag, uint32_t v) {
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (!b) return;
+  const uint32_t lane = lane_id();
+  uint32_t base = 0;
+  if (lane == 0) {
+    if (*(volatile uint32_t*)&c->fq_over[p]) base = 0xffffffffu;
+    else {
+      base = atomicAdd(&c->fq_n[p], uint32_t(__popc(b)));
+      if (base + uint32_t(__popc(b)) > s.fq_limit) { atomicExch(&c->fq_over[p], 1u); base = 0xffffffffu; }
+    }
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (flag && base != 0xffffffffu) s.fq[p][base + __popc(b & ((1u << lane) - 1u))] = v;
+}
+
 // Initialisation (Section 4.2.1): keyword nodes get h = 0 and become frontiers.
 __global__ void k_seed(DevKG g, DevSlot s, int run) {
-  if (s.ctl->done) return;
+  Ctl* c = s.ctl;
+  if (c->done) return;
   const QueryDev& q = *s.q;
   const int nt = run == 0 ? q.n_c : q.n_m;
   const int kb = run == 0 ? 0 : q.n_c;
@@ -124,7 +149,7 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
     const int32_t kw = q.kw[kb + j];
     if (kw < 0 || kw >= g.n_kw) {
       beg[j] = len[j] = 0;
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&s.ctl->err, kErrKeyword);
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrKeyword);
       continue;
     }
     beg[j] = g.kw_ptr[kw];
@@ -132,39 +157,57 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
     total += len[j];
   }
   uint32_t* F0 = s.F[0];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    uint32_t r = i;
-    int j = 0;
-    while (r >= len[j]) { r -= len[j]; ++j; }
-    const int32_t v = g.kw_nodes[beg[j] + r];
-    if (v < 0 || v >= g.n) { atomicOr(&s.ctl->err, kErrInternal); continue; }
-    s.H[size_t(v) * 8 + j] = 0;
-    vis_or(s.vis, uint32_t(v), 1u << j);
-    atomicOr(F0 + (v >> 5), 1u << (v & 31));
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t end = (total + 31u) & ~31u;            // whole warps for the queue push
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+    bool fresh = false;
+    uint32_t v = 0;
+    if (i < total) {
+      uint32_t r = i;
+      int j = 0;
+      while (r >= len[j]) { r -= len[j]; ++j; }
+      const int32_t vv = g.kw_nodes[beg[j] + r];
+      if (vv >= 0 && vv < g.n) {
+        v = uint32_t(vv);
+        s.H[size_t(j) * s.hp + v] = 0;
+        vis_or(s.vis, v, 1u << j);
+        const uint32_t old = atomicOr(F0 + (v >> 5), 1u << (v & 31));
+        fresh = !((old >> (v & 31)) & 1u);
+      } else {
+        atomicOr(&c->err, kErrInternal);
+      }
+    }
+    queue_push(s, c, 0, fresh, v);
   }
 }
 
 // ---------------------------------------------------------- level: enqueue
-// Frontier enqueue (Section 4.2.2): every set bit of F_l is taken and cleared.
+// Frontier enqueue (Section 4.2.2): every node of F_l is taken and its flag
+// cleared - from the frontier queue when it is short (work proportional to
+// |Q_l|), otherwise by scanning the bitmap (lane = node of a 32-bit word).
 // Identification (Section 4.2.3): central run, a node reached by all central
 // keywords is a CG with S^c = max_j h (Theorem 3) and stops expanding;
 // marginal run with |M| >= 2, a node reached by all marginal keywords stops
 // (PTC).  Nodes still expanding become work items with their newly active
-// segment; retained nodes (an edge with a > l) are set in F_{l+1}.  Block 0
-// of the marginal run also performs the RPG identification of the level.
-// Lane = node, items compacted by warp ballots and one 64-bit atomicAdd per
-// block tile of kEnqRounds * 8 words.
+// segment; retained nodes (an edge with a > l) go to F_{l+1}.  Block 0 of
+// the marginal run also performs the RPG identification of the level.
+// Items are compacted with warp ballots, a block scan and one 64-bit
+// atomicAdd per block tile; each item also marks the warp tiles of the
+// expansion that start inside it.
 __global__ void __launch_bounds__(kEnqThreads)
-k_enqueue(DevKG g, DevSlot s, int run, int l) {
+k_enqueue(DevKG g, DevSlot s, int run) {
   Ctl* c = s.ctl;
   if (c->done) return;
+  const uint32_t l = c->lvl_enq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
   const QueryDev& q = *s.q;
   const int nt = run == 0 ? q.n_c : q.n_m;
   const uint32_t full = (1u << nt) - 1u;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   constexpr uint32_t nwarp = kEnqThreads / 32;
-  uint32_t* Fc = s.F[l & 1];
-  uint32_t* Fn = s.F[(l + 1) & 1];
+  const int p = int(l & 1u);
+  uint32_t* Fc = s.F[p];
+  uint32_t* Fn = s.F[p ^ 1];
   __shared__ uint64_t s_warp[33];
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_acc[kMaxK];
@@ -177,8 +220,8 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
     __syncthreads();
     const uint32_t nvc = min(c->nvc, s.cap);
     for (uint32_t i = threadIdx.x; i < nvc; i += blockDim.x) {
-      const uint32_t p = s.vcl[i];
-      atomicOr(&s_acc[p >> kNodeBits], vis_byte(s.vis, p & kNodeMask));
+      const uint32_t pr = s.vcl[i];
+      atomicOr(&s_acc[pr >> kNodeBits], vis_byte(s.vis, pr & kNodeMask));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -191,54 +234,65 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
     }
   }
 
+  const bool sparse = !c->fq_over[p] && c->fq_n[p] <= s.fq_limit;
   const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
+  const uint32_t nsrc = sparse ? c->fq_n[p] : nwords * 32u;   // candidate slots
+  constexpr uint32_t kTile = kEnqThreads * kEnqRounds;        // slots per block tile
   uint32_t qcount = 0;
-  for (uint32_t tile = blockIdx.x * (nwarp * kEnqRounds); tile < nwords; tile += gridDim.x * (nwarp * kEnqRounds)) {
+  for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
     uint32_t it_node[kEnqRounds], it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
-    uint32_t words[kEnqRounds];
+    // candidate node of each round: bitmap mode, word tile/32 + r*nwarp + warp
+    // with lane = bit; queue mode, entry tile + r*blockDim + threadIdx
+    uint32_t cand[kEnqRounds];
+    bool has_r[kEnqRounds];
 #pragma unroll
-    for (int r = 0; r < kEnqRounds; ++r) {          // independent loads first
-      const uint32_t widx = tile + r * nwarp + warp;
-      words[r] = widx < nwords ? Fc[widx] : 0u;
+    for (int r = 0; r < kEnqRounds; ++r) {
+      if (sparse) {
+        const uint32_t i = tile + r * kEnqThreads + threadIdx.x;
+        has_r[r] = i < nsrc;
+        cand[r] = has_r[r] ? s.fq[p][i] : 0u;
+      } else {
+        const uint32_t widx = tile / 32u + r * nwarp + warp;
+        const uint32_t word = widx < nwords ? Fc[widx] : 0u;
+        has_r[r] = (word >> lane) & 1u;
+        cand[r] = widx * 32u + lane;
+        if (lane == 0 && word) Fc[widx] = 0;           // reset F for its next use
+      }
     }
     uint32_t my_items = 0, my_work = 0;
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
       it_len[r] = 0;
       it_node[r] = 0; it_seg[r] = 0; it_msk[r] = 0;
-      const uint32_t widx = tile + r * nwarp + warp;
-      const uint32_t word = words[r];
-      if (word == 0) continue;                      // same word in every lane
-      if (lane == 0) Fc[widx] = 0;                  // reset F for its next use
-      const uint32_t v = widx * 32 + lane;
-      const bool has = (word >> lane) & 1u;
+      const bool has = has_r[r];
+      if (!__any_sync(0xffffffffu, has)) continue;
+      const uint32_t v = cand[r];
+      if (sparse && has) Fc[v >> 5] = 0;               // every set bit of F_l is in the queue
       qcount += has;
       if (s.qlog && has) {
-        const uint32_t p = atomicAdd(&c->qlog_n, 1u);
-        if (p < s.qcap) s.qlog[p] = (uint32_t(l) << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
+        const uint32_t pq = atomicAdd(&c->qlog_n, 1u);
+        if (pq < s.qcap) s.qlog[pq] = (l << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
       }
-      bool stop_now = false, expand = false, is_cg = false;
+      bool expand = false, is_cg = false;
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
-      if (has && !((s.cf[widx] >> lane) & 1u)) {
+      if (has && !((s.cf[v >> 5] >> (v & 31u)) & 1u)) {
         const uint32_t vb = vis_byte(s.vis, v);
-        const uint2 hr = *reinterpret_cast<const uint2*>(s.H + size_t(v) * 8);
-        const uint32_t hb[2] = {hr.x, hr.y};
         uint32_t mx = 0;
         for (int j = 0; j < nt; ++j) {
           if (!((vb >> j) & 1u)) continue;
-          const uint32_t h = (hb[j >> 2] >> ((j & 3) * 8)) & 0xffu;
+          const uint32_t h = s.H[size_t(j) * s.hp + v];
           mx = h > mx ? h : mx;
-          if (h == uint32_t(l)) eq |= uint8_t(1u << j);
-          else if (h < uint32_t(l)) lt |= uint8_t(1u << j);
+          if (h == l) eq |= uint8_t(1u << j);
+          else if (h < l) lt |= uint8_t(1u << j);
         }
         if ((vb & full) == full && (run == 0 || nt >= 2)) {
-          stop_now = true;
           s.stopl[v] = uint8_t(l);
+          atomicOr(s.cf + (v >> 5), 1u << (v & 31u));
           if (run == 0) {
             is_cg = true;
             cg_key = (mx << kNodeBits) | v;
-            if (mx != uint32_t(l)) atomicOr(&c->err, kErrInternal);
+            if (mx != l) atomicOr(&c->err, kErrInternal);
           }
         } else {
           expand = true;
@@ -251,29 +305,26 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if (is_cg) s.cg[base + __popc(cgb & ((1u << lane) - 1u))] = cg_key;
       }
-      const unsigned stopb = __ballot_sync(0xffffffffu, stop_now);
-      if (lane == 0 && stopb) s.cf[widx] |= stopb;     // only this warp owns word widx here
       bool retain = false;
       if (expand) {
-        retain = g.amax[v] > uint32_t(l);
         const uint32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
-        const uint32_t hi = seg_at(g, v, rb, re, uint32_t(l) + 1u);
-        const uint32_t lo = eq ? rb : seg_at(g, v, rb, hi, uint32_t(l));
+        const uint32_t hi = seg_at(g, v, rb, re, l + 1u);
+        const uint32_t lo = eq ? rb : seg_at(g, v, rb, hi, l);
+        retain = hi < re;                              // an edge with a > l remains
         if (hi > lo) {
           it_node[r] = v; it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
           ++my_items;
           my_work += hi - lo;
         }
       }
-      const unsigned retb = __ballot_sync(0xffffffffu, retain);
-      if (lane == 0 && retb) Fn[widx] = retb;          // F_{l+1} word is zero before this level
+      if (retain) atomicOr(Fn + (v >> 5), 1u << (v & 31u));   // F_{l+1} is empty before this level
+      queue_push(s, c, p ^ 1, retain, v);
     }
     if (!__syncthreads_or(my_items != 0)) continue;    // no item in this tile
-    // block-level compaction of the items of this tile
     const uint64_t packed = (uint64_t(my_items) << kWorkBits) | my_work;
     uint64_t tot = 0;
     const uint64_t pre = block_excl_scan(packed, s_warp, &tot);
-    if (threadIdx.x == 0) s_base = atomicAdd(&c->work[l & 1], (unsigned long long)tot);
+    if (threadIdx.x == 0) s_base = atomicAdd(&c->work[p], (unsigned long long)tot);
     __syncthreads();
     if (my_items) {
       uint32_t idx = uint32_t((s_base >> kWorkBits) + (pre >> kWorkBits));
@@ -285,8 +336,7 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
         it.node = it_node[r]; it.seg_begin = it_seg[r]; it.off = off;
         it.eq = uint8_t(it_msk[r]); it.lt = uint8_t(it_msk[r] >> 8); it.pad = 0;
         s.items[idx] = it;
-        // warp tiles of the expansion whose first unit lies in this item
-        const uint32_t last = off + it_len[r] - 1;
+        const uint32_t last = off + it_len[r] - 1;     // warp tiles starting inside the item
         for (uint32_t t = (off + kWarpTile - 1) / kWarpTile; t <= last / kWarpTile; ++t) {
           if (t < s.tile_cap) s.tile_first[t] = idx; else atomicOr(&c->err, kErrOverflow);
         }
@@ -297,7 +347,7 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
     __syncthreads();
   }
   const uint64_t qt = block_sum(qcount, s_warp);
-  if (threadIdx.x == 0 && qt) atomicAdd(&c->nq[l & 1], uint32_t(qt));
+  if (threadIdx.x == 0 && qt) atomicAdd(&c->nq[p], uint32_t(qt));
 }
 
 // ----------------------------------------------------------- level: expand
@@ -309,7 +359,8 @@ k_enqueue(DevKG g, DevSlot s, int run, int l) {
 // lanes of each round read 32 consecutive CSR entries.  Each lane finds its
 // item from a window of 32 items held in registers (one per lane): the item
 // starts inside the round are OR-reduced into a bit mask and a popcount
-// gives the lane's item, so no barrier and no search are needed.
+// gives the lane's item, so no barrier and no search are needed.  When the
+// kernel runs inside a graph WHILE node, block 0 ends the loop as the run stops.
 __device__ __forceinline__ void load_window(const Item* items, uint32_t n_items, uint32_t wb, uint32_t lane,
                                             uint32_t& woff, uint32_t& wseg, uint32_t& wmsk) {
   const uint32_t j = wb + lane;
@@ -322,35 +373,45 @@ __device__ __forceinline__ void load_window(const Item* items, uint32_t n_items,
 }
 
 __global__ void __launch_bounds__(kExpThreads)
-k_expand(DevKG g, DevSlot s, int run, int l) {
+k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
   Ctl* c = s.ctl;
-  if (c->done) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->iters[run] += 1;
+  if (c->done) {
+    if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
+    return;
+  }
   const QueryDev& q = *s.q;
-  const unsigned long long wk = c->work[l & 1];
+  const uint32_t l = c->lvl_exp;
+  const int p = int(l & 1u);
+  const unsigned long long wk = c->work[p];
   const uint32_t n_items = uint32_t(wk >> kWorkBits);
   const uint32_t n_work = uint32_t(wk & kWorkMask);
-  const uint32_t nq = c->nq[l & 1];
+  const uint32_t nq = c->nq[p];
   const bool term = run == 0 ? (c->ncg >= uint32_t(q.k)) : (c->n_matched >= c->nsel);
-  const bool stop = (nq == 0) || term || (l >= q.L);
+  const bool stop = (nq == 0) || term || (l >= uint32_t(q.L));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    c->level = uint32_t(l);
+    c->level = l;
     c->frontier += nq;
-    if (!stop) { c->units += n_work; c->items += n_items; }
     if (stop) {
       c->done = 1;
-      c->levels[run] = (nq == 0 && l > 0) ? l - 1 : l;
+      c->levels[run] = (nq == 0 && l > 0) ? int32_t(l) - 1 : int32_t(l);
+      if (in_graph) cudaGraphSetConditional(loop, 0);
     } else {
-      c->last_expanded = l;
-      c->levels[run] = l;          // provisional; final when the run stops
-      c->work[(l + 1) & 1] = 0;
-      c->nq[(l + 1) & 1] = 0;
+      c->units += n_work;
+      c->items += n_items;
+      c->last_expanded = int32_t(l);
+      c->levels[run] = int32_t(l);   // provisional; final when the run stops
+      c->lvl_enq = l + 1;
+      c->work[p ^ 1] = 0;            // counters of level l+1 (nothing reads them now)
+      c->nq[p ^ 1] = 0;
+      c->fq_n[p] = 0;                // queue of level l was consumed by k_enqueue
+      c->fq_over[p] = 0;
     }
   }
   if (stop || n_work == 0) return;
 
   __shared__ uint64_t s_warp[33];
-  uint32_t* Fn = s.F[(l + 1) & 1];
-  const uint32_t lv = uint32_t(l);
+  uint32_t* Fn = s.F[p ^ 1];
   const uint32_t lane = lane_id();
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -369,8 +430,7 @@ k_expand(DevKG g, DevSlot s, int run, int l) {
       const uint32_t u0 = t0 + 32u * r;
       v_r[r] = false; e_r[r] = 0; m_r[r] = 0;
       if (u0 >= t1) continue;                      // same in every lane
-      // re-base the window so that lane 0 holds the item containing u0
-      for (;;) {
+      for (;;) {                                   // lane 0 must hold the item containing u0
         const unsigned le = __ballot_sync(0xffffffffu, woff <= u0);
         const int hb = 31 - __clz(le);
         if (hb == 0) break;
@@ -394,23 +454,27 @@ k_expand(DevKG g, DevSlot s, int run, int l) {
     for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) {
-      if (!v_r[r]) continue;
-      const uint32_t a = x_r[r] >> kNodeBits;
+      bool fresh = false;
       const uint32_t nb = x_r[r] & kNodeMask;
-      const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
-      const uint32_t act = a < lv ? eq : (eq | lt);   // columns for which the edge is new at level l
-      eact += __popc(act);
-      const uint32_t nw = act & ~vb_r[r];
-      if (nw) {
-        const uint32_t sh = (nb & 3u) * 8u;
-        const uint32_t old = atomicOr(s.vis + (nb >> 2), nw << sh);
-        const uint32_t won = nw & ~(old >> sh) & 0xffu;
-        if (won) {
-          for (uint32_t m = won; m; m &= m - 1) s.H[size_t(nb) * 8 + (__ffs(m) - 1)] = uint8_t(lv + 1);
-          atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
-          hits += __popc(won);
+      if (v_r[r]) {
+        const uint32_t a = x_r[r] >> kNodeBits;
+        const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
+        const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
+        eact += __popc(act);
+        const uint32_t nw = act & ~vb_r[r];
+        if (nw) {
+          const uint32_t sh = (nb & 3u) * 8u;
+          const uint32_t old = atomicOr(s.vis + (nb >> 2), nw << sh);
+          const uint32_t won = nw & ~(old >> sh) & 0xffu;
+          if (won) {
+            for (uint32_t m = won; m; m &= m - 1) s.H[size_t(__ffs(m) - 1) * s.hp + nb] = uint8_t(l + 1);
+            const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
+            fresh = !((of >> (nb & 31u)) & 1u);
+            hits += __popc(won);
+          }
         }
       }
+      queue_push(s, c, p ^ 1, fresh, nb);
     }
   }
   const uint64_t te = block_sum(eact, s_warp);
@@ -518,7 +582,7 @@ k_recover_cols(DevKG g, DevSlot s) {
       const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
       if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
     }
-    if (s.H[size_t(v) * 8 + j] == 0) continue;   // the CG node holds keyword j
+    if (s.H[size_t(j) * s.hp + v] == 0) continue;   // the CG node holds keyword j
     const unsigned long long old = atomicOr(&rmask[v], 1ull << gi);
     if (old == 0) rlist[atomicAdd(&s_n, 1u)] = v;
   }
@@ -533,7 +597,7 @@ k_recover_cols(DevKG g, DevSlot s) {
       unsigned long long m = 0;
       if (i < cnt) {
         const uint32_t qn = rlist[i];
-        if (s.H[size_t(qn) * 8 + j] == uint8_t(x)) {
+        if (s.H[size_t(j) * s.hp + qn] == uint8_t(x)) {
           rb = g.row_ptr[qn];
           len = seg_at(g, qn, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
           m = rmask[qn];
@@ -554,7 +618,7 @@ k_recover_cols(DevKG g, DevSlot s) {
         const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
         const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
         if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
-        const uint32_t hn = s.H[size_t(nb) * 8 + j];
+        const uint32_t hn = s.H[size_t(j) * s.hp + nb];
         const uint32_t lam = a > hn ? a : hn;
         if (lam + 1 != uint32_t(x)) continue;                               // not tight
         if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
@@ -591,7 +655,7 @@ __global__ void k_recover_vc(DevSlot s) {
     s.vmask[v] = 0;
     const uint32_t vb = vis_byte(s.vis, v);
     bool holds = false;
-    for (int j = 0; j < nc; ++j) holds |= ((vb >> j) & 1u) && s.H[size_t(v) * 8 + j] == 0;
+    for (int j = 0; j < nc; ++j) holds |= ((vb >> j) & 1u) && s.H[size_t(j) * s.hp + v] == 0;
     if (!holds) continue;
     for (; m; m &= m - 1) {
       const uint32_t gi = __ffsll(m) - 1;
@@ -671,30 +735,65 @@ int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
-// One run: reset, seed, then L+1 levels of enqueue + expand.
-static void launch_run(const DevKG& g, const DevSlot& s, int run, int L, cudaStream_t st, Prof* prof) {
+// Reset and seed one run.
+void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof) {
   const size_t nwords = (size_t(g.n) + 31) / 32;
-  const int sms = num_sms();
   timed(prof, RPQ_PROF_SETUP, st, [&] {
     k_run_start<<<1, 32, 0, st>>>(s, run);
     cudaMemsetAsync(s.vis, 0, ((size_t(g.n) + 3) / 4) * 4, st);
     cudaMemsetAsync(s.F[0], 0, nwords * 4, st);
     cudaMemsetAsync(s.F[1], 0, nwords * 4, st);
     cudaMemsetAsync(s.cf, 0, nwords * 4, st);
-    k_seed<<<sms * 2, 256, 0, st>>>(g, s, run);
+    k_seed<<<num_sms() * 2, 256, 0, st>>>(g, s, run);
   });
-  const int enq_blocks = int(std::min<size_t>(size_t(sms) * 6, (nwords + 31) / 32 + 1));
-  for (int l = 0; l <= L; ++l) {
-    timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_blocks, kEnqThreads, 0, st>>>(g, s, run, l); });
-    timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, l); });
+}
+
+// One Glevel: enqueue + identification, then termination + expansion.
+void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
+                  cudaGraphConditionalHandle loop, bool in_graph) {
+  const int sms = num_sms();
+  timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<sms * 6, kEnqThreads, 0, st>>>(g, s, run); });
+  timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
+}
+
+// Top-w selection and, when the query has marginal keywords, the recovery.
+void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof) {
+  const int sms = num_sms();
+  timed(prof, RPQ_PROF_TOPK, st, [&] {
+    for (int pass = 0; pass < kTopkPasses; ++pass) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, pass);
+    k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+  });
+  if (n_m > 0) {
+    timed(prof, RPQ_PROF_RECOVER, st, [&] {
+      k_recover_cols<<<kMaxCols, kRecThreads, 0, st>>>(g, s);
+      k_recover_vc<<<sms, 256, 0, st>>>(s);
+    });
   }
 }
 
+void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof) {
+  timed(prof, RPQ_PROF_RESULTS, st, [&] { k_results<<<1, kMaxK, 0, st>>>(s); });
+}
+
+// The whole query without a graph: L+1 level pairs per run.
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
+  launch_run_setup(g, s, 0, st, prof);
+  for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
+  launch_select_recover(g, s, n_m, st, prof);
+  if (n_m > 0) {
+    launch_run_setup(g, s, 1, st, prof);
+    for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
+  }
+  launch_results(s, st, prof);
+  return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
+}
+
 int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof) {
-  launch_run(g, s, 0, L, st, prof);
+  launch_run_setup(g, s, 0, st, prof);
+  for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
   const int sms = num_sms();
   timed(prof, RPQ_PROF_TOPK, st, [&] {
-    for (int p = 0; p < kTopkPasses; ++p) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, p);
+    for (int pass = 0; pass < kTopkPasses; ++pass) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, pass);
     k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
   });
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
@@ -706,21 +805,17 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
       k_recover_cols<<<kMaxCols, kRecThreads, 0, st>>>(g, s);
       k_recover_vc<<<num_sms(), 256, 0, st>>>(s);
     });
-    launch_run(g, s, 1, L, st, prof);
+    launch_run_setup(g, s, 1, st, prof);
+    for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
   }
-  timed(prof, RPQ_PROF_RESULTS, st, [&] { k_results<<<1, kMaxK, 0, st>>>(s); });
+  launch_results(s, st, prof);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
-  const int rc = launch_central_part(g, s, L, st, prof);
-  if (rc != RPQ_OK) return rc;
-  return launch_marginal_part(g, s, n_m, L, st, prof);
-}
-
-// Number of kernels one query launches (for launch accounting).
-int kernels_per_query(int n_m, int L) {
-  const int run = 2 + 2 * (L + 1);            // k_run_start, k_seed, levels
+// Kernels launched by one query in a graph (for launch accounting): fixed
+// kernels plus two per executed Glevel of each run.
+int kernels_fixed_per_query(int n_m) {
+  const int run = 2;                                // k_run_start, k_seed
   return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 2 + run : 0) + 1;
 }
 
