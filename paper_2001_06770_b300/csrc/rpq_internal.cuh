@@ -97,6 +97,7 @@ struct Ctl {
   uint32_t fq_n[2];            // frontier queue lengths per level parity
   uint32_t fq_over[2];         // queue abandoned (frontier too large): use the bitmap
   uint32_t iters[2];           // level kernel pairs executed per run
+  uint32_t fq_use[2];          // the queue of this parity is being filled
   uint32_t n_res;
   uint32_t topk_n[2];          // element counts of the top-k pass buffers
   unsigned long long e_act[2];  // per run

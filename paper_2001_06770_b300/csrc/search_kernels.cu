@@ -112,6 +112,8 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->nq[0] = c->nq[1] = 0;
   c->fq_n[0] = c->fq_n[1] = 0;
   c->fq_over[0] = c->fq_over[1] = 0;
+  c->fq_use[0] = 1;
+  c->fq_use[1] = 0;
   c->lvl_enq = c->lvl_exp = 0;
   c->level = 0;
   c->last_expanded = -1;
@@ -120,7 +122,8 @@ __global__ void k_run_start(DevSlot s, int run) {
 // Append the flagged lanes' nodes to frontier queue p (warp aggregated).  The
 // queue is abandoned (flag set) once it would exceed its limit; the bitmap F
 // stays complete either way.
-__device__ __forceinline__ void queue_push(const DevSlot& s, Ctl* c, int p, bool flag, uint32_t v) {
+__device__ __forceinline__ void queue_push(const DevSlot& s, Ctl* c, int p, bool enabled, bool flag, uint32_t v) {
+  if (!enabled) return;                                  // same in every lane
   const unsigned b = __ballot_sync(0xffffffffu, flag);
   if (!b) return;
   const uint32_t lane = lane_id();
@@ -177,7 +180,7 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
         atomicOr(&c->err, kErrInternal);
       }
     }
-    queue_push(s, c, 0, fresh, v);
+    queue_push(s, c, 0, true, fresh, v);
   }
 }
 
@@ -234,7 +237,12 @@ k_enqueue(DevKG g, DevSlot s, int run) {
     }
   }
 
-  const bool sparse = !c->fq_over[p] && c->fq_n[p] <= s.fq_limit;
+  const bool sparse = c->fq_use[p] && !c->fq_over[p] && c->fq_n[p] <= s.fq_limit;
+  // The next level's queue is kept only while this level is sparse (a dense
+  // level is usually followed by a dense one, and its appends would all
+  // contend on one counter).  Every block computes the same `sparse` from
+  // values no kernel changes during this level; k_expand reads fq_use.
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->fq_use[p ^ 1] = sparse ? 1u : 0u;
   const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
   const uint32_t nsrc = sparse ? c->fq_n[p] : nwords * 32u;   // candidate slots
   constexpr uint32_t kTile = kEnqThreads * kEnqRounds;        // slots per block tile
@@ -273,7 +281,7 @@ k_enqueue(DevKG g, DevSlot s, int run) {
         const uint32_t pq = atomicAdd(&c->qlog_n, 1u);
         if (pq < s.qcap) s.qlog[pq] = (l << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
       }
-      bool expand = false, is_cg = false;
+      bool expand = false, is_cg = false, stop_now = false;
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
       if (has && !((s.cf[v >> 5] >> (v & 31u)) & 1u)) {
@@ -288,7 +296,7 @@ k_enqueue(DevKG g, DevSlot s, int run) {
         }
         if ((vb & full) == full && (run == 0 || nt >= 2)) {
           s.stopl[v] = uint8_t(l);
-          atomicOr(s.cf + (v >> 5), 1u << (v & 31u));
+          stop_now = true;
           if (run == 0) {
             is_cg = true;
             cg_key = (mx << kNodeBits) | v;
@@ -317,8 +325,16 @@ k_enqueue(DevKG g, DevSlot s, int run) {
           my_work += hi - lo;
         }
       }
-      if (retain) atomicOr(Fn + (v >> 5), 1u << (v & 31u));   // F_{l+1} is empty before this level
-      queue_push(s, c, p ^ 1, retain, v);
+      if (sparse) {                                     // nodes of a warp lie in different words
+        if (stop_now) atomicOr(s.cf + (v >> 5), 1u << (v & 31u));
+        if (retain) atomicOr(Fn + (v >> 5), 1u << (v & 31u));
+      } else {                                          // the warp owns word v >> 5: one update each
+        const unsigned sb = __ballot_sync(0xffffffffu, stop_now);
+        const unsigned rb = __ballot_sync(0xffffffffu, retain);
+        if (lane == 0 && sb) atomicOr(s.cf + (v >> 5), sb);
+        if (lane == 0 && rb) atomicOr(Fn + (v >> 5), rb);   // F_{l+1} is empty before this level
+      }
+      queue_push(s, c, p ^ 1, sparse, retain, v);
     }
     if (!__syncthreads_or(my_items != 0)) continue;    // no item in this tile
     const uint64_t packed = (uint64_t(my_items) << kWorkBits) | my_work;
@@ -412,6 +428,7 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
 
   __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[p ^ 1];
+  const bool use_next = c->fq_use[p ^ 1] != 0;   // set by k_enqueue of this level
   const uint32_t lane = lane_id();
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -474,7 +491,7 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
           }
         }
       }
-      queue_push(s, c, p ^ 1, fresh, nb);
+      queue_push(s, c, p ^ 1, use_next, fresh, nb);
     }
   }
   const uint64_t te = block_sum(eact, s_warp);
