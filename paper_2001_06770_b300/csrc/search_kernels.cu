@@ -245,7 +245,9 @@ k_enqueue(DevKG g, DevSlot s, int run) {
   if (blockIdx.x == 0 && threadIdx.x == 0) c->fq_use[p ^ 1] = sparse ? 1u : 0u;
   const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
   const uint32_t nsrc = sparse ? c->fq_n[p] : nwords * 32u;   // candidate slots
-  constexpr uint32_t kTile = kEnqThreads * kEnqRounds;        // slots per block tile
+  // slots per block tile: one round per thread for the queue (short frontiers
+  // spread over many blocks), kEnqRounds words per warp for the bitmap
+  const uint32_t kTile = sparse ? uint32_t(kEnqThreads) : uint32_t(kEnqThreads * kEnqRounds);
   uint32_t qcount = 0;
   for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
     uint32_t it_node[kEnqRounds], it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
@@ -256,8 +258,8 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
       if (sparse) {
-        const uint32_t i = tile + r * kEnqThreads + threadIdx.x;
-        has_r[r] = i < nsrc;
+        const uint32_t i = tile + threadIdx.x;
+        has_r[r] = r == 0 && i < nsrc;
         cand[r] = has_r[r] ? s.fq[p][i] : 0u;
       } else {
         const uint32_t widx = tile / 32u + r * nwarp + warp;
@@ -284,12 +286,25 @@ k_enqueue(DevKG g, DevSlot s, int run) {
       bool expand = false, is_cg = false, stop_now = false;
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
-      if (has && !((s.cf[v >> 5] >> (v & 31u)) & 1u)) {
-        const uint32_t vb = vis_byte(s.vis, v);
+      // every load of the node first (they are independent), then the logic
+      uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
+      uint32_t hv[kMaxCols];
+      if (has) {
+        cfw = s.cf[v >> 5];
+        vb = vis_byte(s.vis, v);
+        rb = g.row_ptr[v];
+        re = g.row_ptr[v + 1];
+#pragma unroll
+        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? s.H[size_t(j) * s.hp + v] : 0u;
+        if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
+        if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
+      }
+      if (has && !((cfw >> (v & 31u)) & 1u)) {
         uint32_t mx = 0;
-        for (int j = 0; j < nt; ++j) {
-          if (!((vb >> j) & 1u)) continue;
-          const uint32_t h = s.H[size_t(j) * s.hp + v];
+#pragma unroll
+        for (int j = 0; j < kMaxCols; ++j) {
+          if (j >= nt || !((vb >> j) & 1u)) continue;
+          const uint32_t h = hv[j];
           mx = h > mx ? h : mx;
           if (h == l) eq |= uint8_t(1u << j);
           else if (h < l) lt |= uint8_t(1u << j);
@@ -315,9 +330,10 @@ k_enqueue(DevKG g, DevSlot s, int run) {
       }
       bool retain = false;
       if (expand) {
-        const uint32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
-        const uint32_t hi = seg_at(g, v, rb, re, l + 1u);
-        const uint32_t lo = eq ? rb : seg_at(g, v, rb, hi, l);
+        const bool indexed = re - rb <= kLvxMaxDeg;
+        const uint32_t hi = (indexed && l + 1 <= kLvxLevels) ? rb + o_hi : seg_lower(g.adj, rb, re, l + 1u);
+        const uint32_t lo = eq ? rb
+                               : (l == 0 ? rb : ((indexed && l <= kLvxLevels) ? rb + o_lo : seg_lower(g.adj, rb, hi, l)));
         retain = hi < re;                              // an edge with a > l remains
         if (hi > lo) {
           it_node[r] = v; it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
@@ -769,7 +785,7 @@ void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st
 void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
                   cudaGraphConditionalHandle loop, bool in_graph) {
   const int sms = num_sms();
-  timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<sms * 6, kEnqThreads, 0, st>>>(g, s, run); });
+  timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<sms * 4, kEnqThreads, 0, st>>>(g, s, run); });
   timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
 }
 
