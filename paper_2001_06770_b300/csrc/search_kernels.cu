@@ -501,8 +501,12 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
           const uint32_t won = nw & ~(old >> sh) & 0xffu;
           if (won) {
             for (uint32_t m = won; m; m &= m - 1) s.H[size_t(__ffs(m) - 1) * s.hp + nb] = uint8_t(l + 1);
-            const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
-            fresh = !((of >> (nb & 31u)) & 1u);
+            if (use_next) {                          // the old word is needed only to fill the queue
+              const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
+              fresh = !((of >> (nb & 31u)) & 1u);
+            } else {
+              atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
+            }
             hits += __popc(won);
           }
         }
