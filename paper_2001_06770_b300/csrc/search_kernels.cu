@@ -485,31 +485,37 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
     uint32_t vb_r[kExpRounds];
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
+    // candidate new columns of every round, then all atomics in flight together
+    uint32_t nw_r[kExpRounds], old_r[kExpRounds];
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) {
+      nw_r[r] = 0;
+      if (!v_r[r]) continue;
+      const uint32_t a = x_r[r] >> kNodeBits;
+      const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
+      const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
+      eact += __popc(act);
+      nw_r[r] = act & ~vb_r[r];
+    }
+#pragma unroll
+    for (int r = 0; r < kExpRounds; ++r) {
+      const uint32_t nb = x_r[r] & kNodeMask;
+      old_r[r] = nw_r[r] ? atomicOr(s.vis + (nb >> 2), nw_r[r] << ((nb & 3u) * 8u)) : 0u;
+    }
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) {
       bool fresh = false;
       const uint32_t nb = x_r[r] & kNodeMask;
-      if (v_r[r]) {
-        const uint32_t a = x_r[r] >> kNodeBits;
-        const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
-        const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
-        eact += __popc(act);
-        const uint32_t nw = act & ~vb_r[r];
-        if (nw) {
-          const uint32_t sh = (nb & 3u) * 8u;
-          const uint32_t old = atomicOr(s.vis + (nb >> 2), nw << sh);
-          const uint32_t won = nw & ~(old >> sh) & 0xffu;
-          if (won) {
-            for (uint32_t m = won; m; m &= m - 1) s.H[size_t(__ffs(m) - 1) * s.hp + nb] = uint8_t(l + 1);
-            if (use_next) {                          // the old word is needed only to fill the queue
-              const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
-              fresh = !((of >> (nb & 31u)) & 1u);
-            } else {
-              atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
-            }
-            hits += __popc(won);
-          }
+      const uint32_t won = nw_r[r] & ~(old_r[r] >> ((nb & 3u) * 8u)) & 0xffu;
+      if (won) {
+        for (uint32_t m = won; m; m &= m - 1) s.H[size_t(__ffs(m) - 1) * s.hp + nb] = uint8_t(l + 1);
+        if (use_next) {                              // the old word is needed only to fill the queue
+          const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
+          fresh = !((of >> (nb & 31u)) & 1u);
+        } else {
+          atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
         }
+        hits += __popc(won);
       }
       queue_push(s, c, p ^ 1, use_next, fresh, nb);
     }
@@ -785,12 +791,24 @@ void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st
   });
 }
 
+// Grid of a persistent-style kernel: SMs x blocks resident per SM (one wave).
+template <typename K>
+static int one_wave_grid(K kernel, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return num_sms() * per_sm;
+}
+
 // One Glevel: enqueue + identification, then termination + expansion.
 void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
                   cudaGraphConditionalHandle loop, bool in_graph) {
-  const int sms = num_sms();
-  timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<sms * 4, kEnqThreads, 0, st>>>(g, s, run); });
-  timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<sms * 8, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
+  static const int enq_grid = one_wave_grid(k_enqueue, kEnqThreads);
+  static const int exp_grid = one_wave_grid(k_expand, kExpThreads);
+  timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_grid, kEnqThreads, 0, st>>>(g, s, run); });
+  timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<exp_grid, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
 }
 
 // Top-w selection and, when the query has marginal keywords, the recovery.
