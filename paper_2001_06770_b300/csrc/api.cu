@@ -57,6 +57,14 @@ struct Slot {
   int32_t pending_nm = 0;
 };
 
+// RPQ_GRAPH_LOOP=0 builds a flat graph (L+1 level pairs per run, finished
+// levels return at once) instead of the WHILE-node graph.
+static bool graph_loops() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_GRAPH_LOOP"); v = (e && *e == '0') ? 0 : 1; }
+  return v == 1;
+}
+
 static bool use_graphs() {
   static int v = -1;
   if (v < 0) { const char* e = getenv("RPQ_NO_GRAPH"); v = (e && *e && *e != '0') ? 0 : 1; }
@@ -249,13 +257,31 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
     return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof);
   }
   (void)n_c;
-  (void)L;   // the graph's loops run as many levels as the query needs
-  const uint64_t key = uint64_t(n_m > 0 ? 1 : 0);
+  // a loop graph depends only on whether the query has marginal keywords; a
+  // flat graph also on L
+  const bool loops = graph_loops();
+  const uint64_t key = loops ? uint64_t(n_m > 0 ? 1 : 0) : ((uint64_t(L) << 8) | uint64_t(n_m > 0 ? 3 : 2));
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
     cudaGraphExec_t exec = nullptr;
-    const int rc = build_query_graph(kg, s, n_m, &exec);
-    if (rc != RPQ_OK) return rc;
+    if (loops) {
+      const int rc = build_query_graph(kg, s, n_m, &exec);
+      if (rc != RPQ_OK) return rc;
+    } else {
+      cudaGraph_t graph = nullptr;
+      RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+      const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr);
+      const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+      if (rc != RPQ_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        set_error(RPQ_ECUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        return RPQ_ECUDA;
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) { set_error(RPQ_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie)); return RPQ_ECUDA; }
+    }
     it = s->graphs.emplace(key, exec).first;
   }
   RPQ_CUDA(cudaGraphLaunch(it->second, s->st));

@@ -444,7 +444,11 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
 
   __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[p ^ 1];
-  const bool use_next = c->fq_use[p ^ 1] != 0;   // set by k_enqueue of this level
+  // The next level's queue (started by k_enqueue of this level) is kept only
+  // if this level's work is small; a large level would overflow it anyway and
+  // its appends would contend on one counter.
+  const bool use_next = c->fq_use[p ^ 1] != 0 && n_work <= 16u * s.fq_limit;
+  if (c->fq_use[p ^ 1] && !use_next && blockIdx.x == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
   const uint32_t lane = lane_id();
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
