@@ -57,12 +57,17 @@ struct Slot {
   int32_t pending_nm = 0;
 };
 
-// RPQ_GRAPH_LOOP=0 builds a flat graph (L+1 level pairs per run, finished
-// levels return at once) instead of the WHILE-node graph.
-static bool graph_loops() {
-  static int v = -1;
-  if (v < 0) { const char* e = getenv("RPQ_GRAPH_LOOP"); v = (e && *e == '0') ? 0 : 1; }
-  return v == 1;
+// Graph form of a query: a flat graph launches L+1 level pairs per run
+// (levels after the run stopped return at once); a loop graph runs the level
+// pair in a WHILE node as often as needed.  On B300 one WHILE iteration costs
+// more than two early-exit launches, so the flat form is used up to
+// kFlatGraphMaxDepth (RPQ_GRAPH_LOOP=1 / 0 forces loops / flat graphs).
+constexpr int kFlatGraphMaxDepth = 12;
+
+static bool graph_loops(int L) {
+  static int v = -2;
+  if (v == -2) { const char* e = getenv("RPQ_GRAPH_LOOP"); v = (e && *e) ? (*e == '0' ? 0 : 1) : -1; }
+  return v == -1 ? (L > kFlatGraphMaxDepth) : (v == 1);
 }
 
 static bool use_graphs() {
@@ -259,7 +264,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
   (void)n_c;
   // a loop graph depends only on whether the query has marginal keywords; a
   // flat graph also on L
-  const bool loops = graph_loops();
+  const bool loops = graph_loops(L);
   const uint64_t key = loops ? uint64_t(n_m > 0 ? 1 : 0) : ((uint64_t(L) << 8) | uint64_t(n_m > 0 ? 3 : 2));
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
