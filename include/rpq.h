@@ -241,6 +241,45 @@ typedef struct {
 int rpq_set_profiling(rpq_kg *kg, int32_t enable);
 int rpq_profile_read(rpq_kg *kg, rpq_profile *out, int32_t reset);
 
+/* --------------------------------------------------------------- serving */
+/* A server runs queries with continuous batching: it owns search slots (the
+ * device state of one in-flight query each, about 60 bytes per graph node
+ * plus the work lists), as many as fit budget_bytes (at least one, at most
+ * max_slots).  A submitted query is admitted as soon as a slot is free and
+ * otherwise waits in arrival order; queries in different slots run
+ * concurrently on the device, each on its own stream.  Each query runs the
+ * same kernels as rpq_search, so its results equal those of rpq_search. */
+typedef struct rpq_server rpq_server;
+
+typedef struct {
+    uint64_t tag;                  /* the tag given at submit (replay: query index) */
+    int32_t status;                /* RPQ_OK or the query's error */
+    int32_t n_res;
+    rpq_result res[RPQ_MAX_K];
+    rpq_stats stats;
+    double latency_s;              /* submit (or scheduled arrival) to completion */
+} rpq_completion;
+
+int rpq_server_create(rpq_kg *kg, int64_t budget_bytes, int32_t max_slots, rpq_server **out);
+int rpq_server_info(const rpq_server *srv, int32_t *n_slots, int64_t *slot_bytes, int32_t *n_running,
+                    int32_t *n_waiting);
+/* Validate and enqueue one query (copied); admits it at once when a slot is
+ * free.  Never waits for the device. */
+int rpq_server_submit(rpq_server *srv, const rpq_query *q, uint64_t tag);
+/* Collect finished queries into out (up to max_done), admitting waiting ones
+ * into freed slots.  wait != 0 blocks until at least one query has finished
+ * (returns at once when nothing is running or waiting). */
+int rpq_server_poll(rpq_server *srv, rpq_completion *out, int32_t max_done, int32_t *n_done, int32_t wait);
+/* Serve an arrival schedule natively: query i is submitted at arrival_s[i]
+ * seconds after the call starts (non-decreasing times).  latency_s[i] counts
+ * from the scheduled arrival to completion; status[i], n_out[i] and (if out is
+ * non-NULL) the results, laid out as in rpq_search_batch, are filled in;
+ * *wall_s receives the elapsed time. */
+int rpq_server_replay(rpq_server *srv, const rpq_query *qs, const double *arrival_s, int32_t nq,
+                      double *latency_s, int32_t *status, int32_t *n_out, rpq_result *out, double *wall_s);
+/* Wait for running queries and release every slot of the server. */
+int rpq_server_destroy(rpq_server *srv);
+
 /* --------------------------------------------- selection without allocation */
 /* rpq_topk_keys_noalloc: write the k smallest of n 32-bit keys, ascending, to
  * d_out and their count (min(k, n)) to *d_n_out.  The paper has no

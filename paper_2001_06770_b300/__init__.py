@@ -28,7 +28,9 @@ MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
            "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
-           "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_strerror", "rpq_last_error"]
+           "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_info",
+           "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
+           "rpq_strerror", "rpq_last_error"]
 PROF_CLASSES = ["setup", "enqueue", "expand", "topk", "recover", "results"]
 
 
@@ -74,6 +76,11 @@ class TraceBuf(ctypes.Structure):
                 ("selected", ctypes.c_int32 * MAX_K), ("n_selected", ctypes.c_int32)]
 
 
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_res", ctypes.c_int32),
+                ("res", ctypes.c_uint8 * (24 * MAX_K)), ("stats", Stats), ("latency_s", ctypes.c_double)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
@@ -107,6 +114,12 @@ def lib():
         L.rpq_set_profiling.argtypes = [P, i32]
         L.rpq_profile_read.argtypes = [P, ctypes.POINTER(Profile), i32]
         L.rpq_topk_keys_noalloc.argtypes = [P, ctypes.c_uint32, i32, P, P, P]
+        L.rpq_server_create.argtypes = [P, i64, i32, ctypes.POINTER(P)]
+        L.rpq_server_info.argtypes = [P, P, P, P, P]
+        L.rpq_server_submit.argtypes = [P, ctypes.POINTER(Query), ctypes.c_uint64]
+        L.rpq_server_poll.argtypes = [P, P, i32, P, i32]
+        L.rpq_server_replay.argtypes = [P, P, P, i32, P, P, P, P, P]
+        L.rpq_server_destroy.argtypes = [P]
         L.rpq_strerror.argtypes = [ctypes.c_int]
         L.rpq_strerror.restype = ctypes.c_char_p
         L.rpq_last_error.restype = ctypes.c_char_p
@@ -273,3 +286,67 @@ class KG:
         p = Profile()
         _check(lib().rpq_profile_read(self._h, ctypes.byref(p), int(bool(reset))))
         return {c: (p.ms[i], p.launches[i]) for i, c in enumerate(PROF_CLASSES)}
+
+
+class Server:
+    """Continuous-batching server over a loaded KG (rpq_server_* in rpq.h)."""
+
+    def __init__(self, kg: KG, budget_bytes: int, max_slots: int = 256):
+        self._h = ctypes.c_void_p()
+        self.kg = kg
+        _check(lib().rpq_server_create(kg._h, int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
+
+    def info(self):
+        n, b, r, w = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().rpq_server_info(self._h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(r), ctypes.byref(w)))
+        return dict(slots=n.value, slot_bytes=b.value, running=r.value, waiting=w.value)
+
+    def submit(self, q, tag: int):
+        keep = []
+        qq = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+        _check(lib().rpq_server_submit(self._h, ctypes.byref(qq), ctypes.c_uint64(tag)))
+
+    def poll(self, wait: bool = False, max_done: int = 256):
+        """List of (tag, status, results, stats, latency_s) of finished queries."""
+        buf = (Completion * max_done)()
+        n = ctypes.c_int32()
+        _check(lib().rpq_server_poll(self._h, ctypes.cast(buf, ctypes.c_void_p), max_done, ctypes.byref(n),
+                                     int(bool(wait))))
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            res = np.frombuffer(bytes(c.res), RESULT_DTYPE)[:c.n_res].copy()
+            out.append((int(c.tag), int(c.status), res, c.stats.as_dict(), float(c.latency_s)))
+        return out
+
+    def replay(self, queries, arrival_s):
+        """Serve the queries at the given arrival times (seconds, non-decreasing)
+        natively; returns (results list, latency_s array, status array, wall_s)."""
+        queries = list(queries)
+        nq = len(queries)
+        keep = []
+        arr = (Query * max(nq, 1))()
+        for i, q in enumerate(queries):
+            arr[i] = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+        t = np.ascontiguousarray(arrival_s, np.float64)
+        lat = np.zeros(max(nq, 1), np.float64)
+        status = np.zeros(max(nq, 1), np.int32)
+        n_out = np.zeros(max(nq, 1), np.int32)
+        base = np.concatenate([[0], np.cumsum([int(q.k) for q in queries])]).astype(np.int64)
+        out = np.zeros(max(int(base[-1]), 1), RESULT_DTYPE)
+        wall = ctypes.c_double()
+        _check(lib().rpq_server_replay(self._h, ctypes.cast(arr, ctypes.c_void_p), _ptr(t), nq, _ptr(lat),
+                                       _ptr(status), _ptr(n_out), _ptr(out), ctypes.byref(wall)))
+        res = [out[base[i]:base[i] + n_out[i]].copy() for i in range(nq)]
+        return res, lat[:nq], status[:nq], wall.value
+
+    def close(self):
+        if self._h:
+            lib().rpq_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -42,21 +42,6 @@ int dev_err_to_status(uint32_t err) {
   return RPQ_EINTERNAL;
 }
 
-// One search slot: device state of one in-flight query, its stream, pinned
-// staging for results and the captured graphs of each query shape.
-struct Slot {
-  DevSlot d{};
-  cudaStream_t st = nullptr;
-  int64_t bytes = 0;
-  Ctl* h_ctl = nullptr;
-  rpq_result* h_res = nullptr;
-  std::vector<void*> allocs;
-  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
-  bool busy = false;
-  int32_t pending_k = 0;
-  int32_t pending_nm = 0;
-};
-
 // Graph form of a query: a flat graph launches L+1 level pairs per run
 // (levels after the run stopped return at once); a loop graph runs the level
 // pair in a WHILE node as often as needed.  On B300 one WHILE iteration costs
@@ -76,7 +61,7 @@ static bool use_graphs() {
   return v == 1;
 }
 
-static void destroy_slot(Slot* s) {
+void destroy_slot(Slot* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
@@ -87,7 +72,7 @@ static void destroy_slot(Slot* s) {
   delete s;
 }
 
-static int create_slot(rpq_kg* kg, Slot** out) {
+int create_slot(rpq_kg* kg, Slot** out) {
   Slot* s = new Slot();
   const size_t n = size_t(kg->dev.n);
   const size_t nwords = (n + 31) / 32;
@@ -148,7 +133,7 @@ static int create_slot(rpq_kg* kg, Slot** out) {
   return RPQ_OK;
 }
 
-static int get_slot(rpq_kg* kg, size_t i, Slot** out) {
+int get_slot(rpq_kg* kg, size_t i, Slot** out) {
   while (kg->slots.size() <= i) {
     Slot* s = nullptr;
     const int rc = create_slot(kg, &s);
@@ -162,7 +147,7 @@ static int get_slot(rpq_kg* kg, size_t i, Slot** out) {
 
 // Host validation of a query; fills qv.  Returns RPQ_OK, or an error, and
 // sets *empty when a keyword has no keyword node (no result is possible).
-static int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty) {
+int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty) {
   if (!q) { set_error(RPQ_EINVAL, "query is NULL"); return RPQ_EINVAL; }
   if (q->n_c < 1 || q->n_c > kMaxCols || q->n_m < 0 || q->n_m > kMaxCols) {
     set_error(RPQ_EINVAL, "need 1 <= n_c <= %d and 0 <= n_m <= %d (got %d, %d)", kMaxCols, kMaxCols, q->n_c, q->n_m);
@@ -294,7 +279,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
 }
 
 // Start a validated query on a slot (asynchronous).
-static int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
+int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
   int rc = launch_query_setup(s->d, qv, nullptr, s->st);
   if (rc != RPQ_OK) { set_error(RPQ_ECUDA, "launch failed: %s", cudaGetErrorString(cudaGetLastError())); return rc; }
   rc = enqueue_body(kg, s, qv.n_c, qv.n_m, qv.L);
@@ -323,7 +308,7 @@ static void fill_stats(const Ctl& c, rpq_stats* st) {
 }
 
 // Wait for the slot's query and copy its results out.
-static int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
+int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
   s->busy = false;
   RPQ_CUDA(cudaStreamSynchronize(s->st));
   if (kg->prof) kg->prof->collect();
@@ -338,7 +323,7 @@ static int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rp
   return RPQ_OK;
 }
 
-static void empty_result(int32_t* n_out, rpq_stats* stats) {
+void empty_result(int32_t* n_out, rpq_stats* stats) {
   if (n_out) *n_out = 0;
   if (stats) {
     memset(stats, 0, sizeof(*stats));

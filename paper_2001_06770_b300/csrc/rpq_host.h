@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cstdio>
+#include <unordered_map>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -24,7 +25,20 @@ int alloc_device(void** p, size_t bytes, int64_t* counter);
     }                                                                                      \
   } while (0)
 
-struct Slot;
+// One search slot: device state of one in-flight query, its stream, pinned
+// staging for results and the graphs captured for each query shape.
+struct Slot {
+  DevSlot d{};
+  cudaStream_t st = nullptr;
+  int64_t bytes = 0;
+  Ctl* h_ctl = nullptr;
+  rpq_result* h_res = nullptr;
+  std::vector<void*> allocs;
+  std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
+  bool busy = false;
+  int32_t pending_k = 0;
+  int32_t pending_nm = 0;
+};
 
 // Optional per-launch timing with CUDA events (profiling mode, no graphs).
 struct Prof {
@@ -75,4 +89,13 @@ struct rpq_kg {
 namespace rpq {
 // Fill d_row_ptr, d_adj and d_amax of kg from the host CSR (kg_build.cu).
 int build_graph(rpq_kg* kg, const rpq_kg_desc* d);
+
+// Search slots and query execution (api.cu).
+int create_slot(rpq_kg* kg, Slot** out);
+void destroy_slot(Slot* s);
+int get_slot(rpq_kg* kg, size_t i, Slot** out);
+int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty);
+int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv);      // asynchronous
+int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats);
+void empty_result(int32_t* n_out, rpq_stats* stats);
 }  // namespace rpq

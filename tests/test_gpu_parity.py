@@ -101,7 +101,12 @@ def tiny():
 def test_k_and_depth_extremes(tiny, k, L):
     ds, act, kg = tiny
     q = rpqgen.Query(central=[124, 464], marginal=[375, 63], k=k, max_depth=L)
-    trace_matches(kg.trace(q.central, q.marginal, k, L), oracle_query(ds, act, q))
+    orc = oracle_query(ds, act, q)
+    trace_matches(kg.trace(q.central, q.marginal, k, L), orc)
+    # graph-replayed search: flat graph for L <= 12, WHILE-loop graph beyond
+    res, st = kg.search(q.central, q.marginal, k, L)
+    results_match(res, orc)
+    assert st["e_act_central"] == orc.central.e_act
 
 
 @pytest.mark.parametrize("C,M", [([30], []), ([124], [375]), ([124, 464, 124], [375]), ([124, 464], [375, 375]),
