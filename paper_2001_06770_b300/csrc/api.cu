@@ -36,6 +36,7 @@ void set_error(int code, const char* fmt, ...) {
 
 int dev_err_to_status(uint32_t err) {
   if (!err) return RPQ_OK;
+  if (err & kErrTimeout) { set_error(RPQ_ETIMEOUT, "a bounded device wait ran out"); return RPQ_ETIMEOUT; }
   if (err & kErrKeyword) { set_error(RPQ_EINVAL, "keyword id out of range (device check)"); return RPQ_EINVAL; }
   if (err & kErrOverflow) { set_error(RPQ_EINTERNAL, "a device work list overflowed"); return RPQ_EINTERNAL; }
   set_error(RPQ_EINTERNAL, "device consistency check failed (flags 0x%x)", err);
@@ -112,12 +113,14 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.q, sizeof(QueryDev));
   SA(d.res, sizeof(rpq_result) * kMaxK);
   SA(d.n_res, 16);
+  SA(d.bar, 16);
 #undef SA
   if (rc == RPQ_OK) {
     // masks start at zero; the recovery kernel restores zero after each use
     if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess ||
         cudaMemset(d.vmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
         cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
+        cudaMemset(d.bar, 0, 16) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl)) != cudaSuccess ||
         cudaMallocHost((void**)&s->h_res, sizeof(rpq_result) * kMaxK) != cudaSuccess) {
@@ -133,11 +136,22 @@ int create_slot(rpq_kg* kg, Slot** out) {
   return RPQ_OK;
 }
 
+// Slot 0 serves one query at a time (rpq_search, rpq_search_device): its
+// level loops run as one persistent cooperative kernel per run, which keeps
+// the whole GPU.  Other slots run concurrently and use separate level
+// kernels.  RPQ_PERSISTENT=0 turns the persistent form off.
+static bool persistent_slot0() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_PERSISTENT"); v = (e && *e == '0') ? 0 : 1; }
+  return v == 1;
+}
+
 int get_slot(rpq_kg* kg, size_t i, Slot** out) {
   while (kg->slots.size() <= i) {
     Slot* s = nullptr;
     const int rc = create_slot(kg, &s);
     if (rc != RPQ_OK) return rc;
+    s->d.persistent = (kg->slots.empty() && persistent_slot0()) ? 1u : 0u;
     kg->slots.push_back(s);
     kg->device_bytes += s->bytes;
   }
@@ -249,7 +263,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
   (void)n_c;
   // a loop graph depends only on whether the query has marginal keywords; a
   // flat graph also on L
-  const bool loops = graph_loops(L);
+  const bool loops = !s->d.persistent && graph_loops(L);
   const uint64_t key = loops ? uint64_t(n_m > 0 ? 1 : 0) : ((uint64_t(L) << 8) | uint64_t(n_m > 0 ? 3 : 2));
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
@@ -319,7 +333,11 @@ int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats
   if (out && nr) memcpy(out, s->h_res, sizeof(rpq_result) * size_t(nr));
   if (n_out) *n_out = nr;
   fill_stats(c, stats);
-  if (stats) stats->kernels = kernels_fixed_per_query(s->pending_nm) + 2 * int64_t(c.iters[0] + c.iters[1]);
+  if (stats) {
+    const int runs = 1 + (s->pending_nm > 0 && c.levels[1] >= 0 ? 1 : 0);
+    stats->kernels = kernels_fixed_per_query(s->pending_nm) +
+                     (s->d.persistent ? runs : 2 * int64_t(c.iters[0] + c.iters[1]));
+  }
   return RPQ_OK;
 }
 
@@ -462,8 +480,8 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
   if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
   const int nslots = std::max(1, std::min<int>(slot_count(), nq));
   std::vector<Slot*> slots(size_t(nslots), nullptr);
-  for (int i = 0; i < nslots; ++i) {
-    const int rc = get_slot(kg, size_t(i), &slots[size_t(i)]);
+  for (int i = 0; i < nslots; ++i) {          // slots 1..nslots: slot 0 serves single searches
+    const int rc = get_slot(kg, size_t(i) + 1, &slots[size_t(i)]);
     if (rc != RPQ_OK) return rc;
   }
   std::vector<int64_t> base(size_t(nq) + 1, 0);

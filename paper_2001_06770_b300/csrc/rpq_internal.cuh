@@ -41,6 +41,7 @@ enum DevErr : uint32_t {
   kErrKeyword = 1u << 5,   // keyword id out of range (device queries)
   kErrOverflow = 1u << 6,  // a work list overflowed its capacity
   kErrInternal = 1u << 7,
+  kErrTimeout = 1u << 8,   // a bounded grid barrier ran out
 };
 
 // Rows with at most kLvxMaxDeg entries carry a level index: lvx[x-1][v] is
@@ -133,6 +134,8 @@ struct DevSlot {
   uint32_t* qlog;             // trace mode: (level << 26 | node) of every Q_l entry
   uint32_t qcap;
   uint32_t* sticky;           // device error bits kept across queries
+  unsigned* bar;              // grid barrier of the persistent run kernel: count, generation
+  uint32_t persistent;        // run each level loop as one cooperative k_run launch
   Ctl* ctl;
   QueryDev* q;
   void* res;                  // rpq_result[kMaxK] on the device

@@ -86,6 +86,15 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* s_warp) {
   return t;  // valid in thread 0
 }
 
+// Load of a value that other blocks may have written earlier in the same
+// kernel: in the persistent kernel (P) it must come from L2, not a possibly
+// stale L1 line; separate kernels may use the cached path.
+template <bool P, typename T>
+__device__ __forceinline__ T ldx(const T* ptr) {
+  if constexpr (P) return __ldcg(ptr);
+  else return *ptr;
+}
+
 __device__ __forceinline__ void vis_or(uint32_t* vis, uint32_t v, uint32_t bits) {
   atomicOr(vis + (v >> 2), bits << ((v & 3u) * 8u));
 }
@@ -116,6 +125,7 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->fq_use[1] = 0;
   c->lvl_enq = c->lvl_exp = 0;
   c->level = 0;
+  s.bar[0] = 0;                      // barrier arrivals of the persistent kernel
   c->last_expanded = -1;
 }
 
@@ -197,12 +207,9 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
 // Items are compacted with warp ballots, a block scan and one 64-bit
 // atomicAdd per block tile; each item also marks the warp tiles of the
 // expansion that start inside it.
-__global__ void __launch_bounds__(kEnqThreads)
-k_enqueue(DevKG g, DevSlot s, int run) {
+template <bool P>
+__device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l) {
   Ctl* c = s.ctl;
-  if (c->done) return;
-  const uint32_t l = c->lvl_enq;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
   const QueryDev& q = *s.q;
   const int nt = run == 0 ? q.n_c : q.n_m;
   const uint32_t full = (1u << nt) - 1u;
@@ -218,13 +225,13 @@ k_enqueue(DevKG g, DevSlot s, int run) {
   if (run == 1 && blockIdx.x == 0) {
     // RPG identification: a selected CG matches when every marginal keyword
     // has reached some node of its V_C; then S^m = max_i min_{v in V_C} h = l.
-    const uint32_t nsel = c->nsel;
+    const uint32_t nsel = ldx<P>(&c->nsel);
     for (uint32_t i = threadIdx.x; i < kMaxK; i += blockDim.x) s_acc[i] = 0;
     __syncthreads();
-    const uint32_t nvc = min(c->nvc, s.cap);
+    const uint32_t nvc = min(ldx<P>(&c->nvc), s.cap);
     for (uint32_t i = threadIdx.x; i < nvc; i += blockDim.x) {
       const uint32_t pr = s.vcl[i];
-      atomicOr(&s_acc[pr >> kNodeBits], vis_byte(s.vis, pr & kNodeMask));
+      atomicOr(&s_acc[pr >> kNodeBits], uint32_t(ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + (pr & kNodeMask))));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -237,14 +244,15 @@ k_enqueue(DevKG g, DevSlot s, int run) {
     }
   }
 
-  const bool sparse = c->fq_use[p] && !c->fq_over[p] && c->fq_n[p] <= s.fq_limit;
+  const uint32_t fq_n = ldx<P>(&c->fq_n[p]);
+  const bool sparse = ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && fq_n <= s.fq_limit;
   // The next level's queue is kept only while this level is sparse (a dense
   // level is usually followed by a dense one, and its appends would all
   // contend on one counter).  Every block computes the same `sparse` from
   // values no kernel changes during this level; k_expand reads fq_use.
   if (blockIdx.x == 0 && threadIdx.x == 0) c->fq_use[p ^ 1] = sparse ? 1u : 0u;
   const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
-  const uint32_t nsrc = sparse ? c->fq_n[p] : nwords * 32u;   // candidate slots
+  const uint32_t nsrc = sparse ? fq_n : nwords * 32u;   // candidate slots
   // slots per block tile: one round per thread for the queue (short frontiers
   // spread over many blocks), kEnqRounds words per warp for the bitmap
   const uint32_t kTile = sparse ? uint32_t(kEnqThreads) : uint32_t(kEnqThreads * kEnqRounds);
@@ -260,10 +268,10 @@ k_enqueue(DevKG g, DevSlot s, int run) {
       if (sparse) {
         const uint32_t i = tile + threadIdx.x;
         has_r[r] = r == 0 && i < nsrc;
-        cand[r] = has_r[r] ? s.fq[p][i] : 0u;
+        cand[r] = has_r[r] ? ldx<P>(s.fq[p] + i) : 0u;
       } else {
         const uint32_t widx = tile / 32u + r * nwarp + warp;
-        const uint32_t word = widx < nwords ? Fc[widx] : 0u;
+        const uint32_t word = widx < nwords ? ldx<P>(Fc + widx) : 0u;
         has_r[r] = (word >> lane) & 1u;
         cand[r] = widx * 32u + lane;
         if (lane == 0 && word) Fc[widx] = 0;           // reset F for its next use
@@ -290,12 +298,12 @@ k_enqueue(DevKG g, DevSlot s, int run) {
       uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
       uint32_t hv[kMaxCols];
       if (has) {
-        cfw = s.cf[v >> 5];
-        vb = vis_byte(s.vis, v);
+        cfw = ldx<P>(s.cf + (v >> 5));
+        vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
         rb = g.row_ptr[v];
         re = g.row_ptr[v + 1];
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? s.H[size_t(j) * s.hp + v] : 0u;
+        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? ldx<P>(s.H + size_t(j) * s.hp + v) : 0u;
         if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
         if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
       }
@@ -382,6 +390,15 @@ k_enqueue(DevKG g, DevSlot s, int run) {
   if (threadIdx.x == 0 && qt) atomicAdd(&c->nq[p], uint32_t(qt));
 }
 
+__global__ void __launch_bounds__(kEnqThreads)
+k_enqueue(DevKG g, DevSlot s, int run) {
+  Ctl* c = s.ctl;
+  if (c->done) return;
+  const uint32_t l = c->lvl_enq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
+  enqueue_level<false>(g, s, run, l);
+}
+
 // ----------------------------------------------------------- level: expand
 // Termination (every block reaches the same decision from the control block,
 // which k_enqueue finished writing) and expansion (Algorithm 1) of the work
@@ -393,33 +410,31 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 // starts inside the round are OR-reduced into a bit mask and a popcount
 // gives the lane's item, so no barrier and no search are needed.  When the
 // kernel runs inside a graph WHILE node, block 0 ends the loop as the run stops.
+template <bool P>
 __device__ __forceinline__ void load_window(const Item* items, uint32_t n_items, uint32_t wb, uint32_t lane,
                                             uint32_t& woff, uint32_t& wseg, uint32_t& wmsk) {
   const uint32_t j = wb + lane;
   if (j < n_items) {
-    const Item it = items[j];
+    const uint4 raw = ldx<P>(reinterpret_cast<const uint4*>(items + j));
+    const Item it = *reinterpret_cast<const Item*>(&raw);
     woff = it.off; wseg = it.seg_begin; wmsk = uint32_t(it.eq) | (uint32_t(it.lt) << 8);
   } else {
     woff = 0xffffffffu; wseg = 0; wmsk = 0;
   }
 }
 
-__global__ void __launch_bounds__(kExpThreads)
-k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
+// Returns true when the run stops at level l (no expansion then).
+template <bool P>
+__device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, int run, uint32_t l,
+                                             cudaGraphConditionalHandle loop, int in_graph) {
   Ctl* c = s.ctl;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->iters[run] += 1;
-  if (c->done) {
-    if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
-    return;
-  }
   const QueryDev& q = *s.q;
-  const uint32_t l = c->lvl_exp;
   const int p = int(l & 1u);
-  const unsigned long long wk = c->work[p];
+  const unsigned long long wk = ldx<P>(&c->work[p]);
   const uint32_t n_items = uint32_t(wk >> kWorkBits);
   const uint32_t n_work = uint32_t(wk & kWorkMask);
-  const uint32_t nq = c->nq[p];
-  const bool term = run == 0 ? (c->ncg >= uint32_t(q.k)) : (c->n_matched >= c->nsel);
+  const uint32_t nq = ldx<P>(&c->nq[p]);
+  const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.k)) : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel));
   const bool stop = (nq == 0) || term || (l >= uint32_t(q.L));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->level = l;
@@ -440,15 +455,16 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
       c->fq_over[p] = 0;
     }
   }
-  if (stop || n_work == 0) return;
+  if (stop || n_work == 0) return stop;
 
   __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[p ^ 1];
   // The next level's queue (started by k_enqueue of this level) is kept only
   // if this level's work is small; a large level would overflow it anyway and
   // its appends would contend on one counter.
-  const bool use_next = c->fq_use[p ^ 1] != 0 && n_work <= 16u * s.fq_limit;
-  if (c->fq_use[p ^ 1] && !use_next && blockIdx.x == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
+  const uint32_t fq_use_next = ldx<P>(&c->fq_use[p ^ 1]);
+  const bool use_next = fq_use_next != 0 && n_work <= 16u * s.fq_limit;
+  if (fq_use_next && !use_next && blockIdx.x == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
   const uint32_t lane = lane_id();
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -457,9 +473,9 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
   for (uint32_t t = gw; t < ntiles; t += nwarps) {
     const uint32_t t0 = t * kWarpTile;
     const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
-    uint32_t wb = s.tile_first[t];
+    uint32_t wb = ldx<P>(s.tile_first + t);
     uint32_t woff, wseg, wmsk;
-    load_window(s.items, n_items, wb, lane, woff, wseg, wmsk);
+    load_window<P>(s.items, n_items, wb, lane, woff, wseg, wmsk);
     uint32_t e_r[kExpRounds], m_r[kExpRounds];
     bool v_r[kExpRounds];
 #pragma unroll
@@ -472,7 +488,7 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
         const int hb = 31 - __clz(le);
         if (hb == 0) break;
         wb += uint32_t(hb);
-        load_window(s.items, n_items, wb, lane, woff, wseg, wmsk);
+        load_window<P>(s.items, n_items, wb, lane, woff, wseg, wmsk);
       }
       const uint32_t bit = (lane > 0 && woff < u0 + 32u) ? (1u << (woff - u0)) : 0u;
       const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
@@ -529,6 +545,65 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
   if (threadIdx.x == 0) {
     if (te) atomicAdd(&c->e_act[run], (unsigned long long)te);
     if (th) atomicAdd(&c->hits[run], (unsigned long long)th);
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(kExpThreads)
+k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
+  Ctl* c = s.ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->iters[run] += 1;
+  if (c->done) {
+    if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
+    return;
+  }
+  expand_level<false>(g, s, run, c->lvl_exp, loop, in_graph);
+}
+
+// ------------------------------------------------------ persistent run kernel
+// All Glevels of one run in one cooperative launch (every block resident):
+// the enqueue and expansion phases of a level are separated by a grid
+// barrier instead of a kernel boundary.  The barrier is bounded: a block that
+// waits longer than kBarrierCycles sets kErrTimeout and every block leaves
+// the kernel at its next barrier, so the kernel always ends.
+constexpr long long kBarrierCycles = 2000000000ll;   // ~1 s at 2 GHz
+
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, uint32_t* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g0 = *(volatile unsigned*)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) + 1u == nblocks) {
+      *(volatile unsigned*)count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*(volatile unsigned*)gen == g0) {
+        if (*(volatile uint32_t*)err & kErrTimeout) { ok = 0; break; }
+        if (clock64() - t0 > kBarrierCycles) { atomicOr(err, kErrTimeout); ok = 0; break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kExpThreads)
+k_run(DevKG g, DevSlot s, int run) {
+  Ctl* c = s.ctl;
+  if (c->done) return;
+  for (;;) {
+    const uint32_t l = *(volatile uint32_t*)&c->lvl_enq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { c->lvl_exp = l; c->iters[run] += 1; }
+    enqueue_level<true>(g, s, run, l);
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) return;
+    if (expand_level<true>(g, s, run, l, 0, 0)) return;
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) return;
   }
 }
 
@@ -806,6 +881,24 @@ static int one_wave_grid(K kernel, int threads) {
   return num_sms() * per_sm;
 }
 
+// One run as a single cooperative launch of k_run (one wave of blocks).
+void launch_run_persistent(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof) {
+  static const int grid = one_wave_grid(k_run, kExpThreads);
+  timed(prof, RPQ_PROF_EXPAND, st, [&] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(kExpThreads));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_run, g, s, run);
+  });
+}
+
 // One Glevel: enqueue + identification, then termination + expansion.
 void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
                   cudaGraphConditionalHandle loop, bool in_graph) {
@@ -834,14 +927,16 @@ void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof) {
   timed(prof, RPQ_PROF_RESULTS, st, [&] { k_results<<<1, kMaxK, 0, st>>>(s); });
 }
 
-// The whole query without a graph: L+1 level pairs per run.
+// The whole query without a graph: one persistent launch or L+1 level pairs per run.
 int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
   launch_run_setup(g, s, 0, st, prof);
-  for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
+  if (s.persistent) launch_run_persistent(g, s, 0, st, prof);
+  else for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
   launch_select_recover(g, s, n_m, st, prof);
   if (n_m > 0) {
     launch_run_setup(g, s, 1, st, prof);
-    for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
+    if (s.persistent) launch_run_persistent(g, s, 1, st, prof);
+    else for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
   }
   launch_results(s, st, prof);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
@@ -872,7 +967,7 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
 }
 
 // Kernels launched by one query in a graph (for launch accounting): fixed
-// kernels plus two per executed Glevel of each run.
+// kernels plus, per run, two per executed Glevel or one persistent launch.
 int kernels_fixed_per_query(int n_m) {
   const int run = 2;                                // k_run_start, k_seed
   return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 2 + run : 0) + 1;
