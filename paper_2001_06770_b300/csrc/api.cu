@@ -136,13 +136,15 @@ int create_slot(rpq_kg* kg, Slot** out) {
   return RPQ_OK;
 }
 
-// Slot 0 serves one query at a time (rpq_search, rpq_search_device): its
-// level loops run as one persistent cooperative kernel per run, which keeps
-// the whole GPU.  Other slots run concurrently and use separate level
-// kernels.  RPQ_PERSISTENT=0 turns the persistent form off.
+// Slot 0 serves one query at a time (rpq_search, rpq_search_device).  With
+// RPQ_PERSISTENT=1 its level loops run as one persistent cooperative kernel
+// per run (grid barriers instead of kernel boundaries).  Measured on B300 it
+// is not faster than kernel pairs replayed from a flat CUDA graph (fewer
+// resident blocks, L2-only loads of cross-block state, two barriers per
+// level), so it is off by default.  Other slots always use kernel pairs.
 static bool persistent_slot0() {
   static int v = -1;
-  if (v < 0) { const char* e = getenv("RPQ_PERSISTENT"); v = (e && *e == '0') ? 0 : 1; }
+  if (v < 0) { const char* e = getenv("RPQ_PERSISTENT"); v = (e && *e == '1') ? 1 : 0; }
   return v == 1;
 }
 
