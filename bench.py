@@ -147,8 +147,9 @@ def run_reference(args):
         return 0
     import oracle
     import rpqgen
-    ds = rpqgen.make_dataset("medium")
-    qs = rpqgen.workload_queries("medium", ds)
+    wl = WORKLOADS[args.workload]
+    ds = rpqgen.make_dataset(wl["ds"])
+    qs = rpqgen.workload_queries(wl["queries"], ds)
     act = oracle.dataset_activation(ds)
     times = []
     for s in range(args.warmup + args.steps):
@@ -162,12 +163,60 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one query of the workload (cycling)"},
+            "config": {"workload": wl["desc"], "step": "one query of the workload (cycling)"},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} queries of the 64, serial C oracle, one core"},
+                             "sample": f"{args.steps} queries of the {len(qs)}, serial C oracle, one core"},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+WORKLOADS = {
+    "medium": dict(ds="medium", queries="medium", mode="single", desc=WORKLOAD),
+    "large": dict(ds="large", queries="large", mode="single",
+                  desc="large: Chung-Lu (exponent 2.1) 5e7 nodes, 4e8 sampled edges, symmetric int32 CSR; "
+                       "256 RPQs one at a time, |C| = |M| = 3, ranks 100-20000, k=20, L=8"),
+    "batched": dict(ds="large", queries="batched", mode="batch",
+                    desc="batched: large graph; 4096 RPQs of uneven shape (|C| 2-6, |M| 0-8, head/tail keywords, "
+                         "k in {5,10,20}, L=8) in one rpq_search_batch call"),
+    "served": dict(ds="medium", queries="served", mode="serve",
+                   desc="served: medium graph; 20000 RPQs (shapes as batched) arriving as a Poisson stream, "
+                        "continuous batching under a 16 GB slot budget"),
+}
+
+
+def expand_roofline(kg, qs, stats):
+    """Profiling pass: device time of each kernel class, and the expansion
+    kernel's algorithmic bytes per second against the measured HBM peak."""
+    kg.set_profiling(True)
+    for q in qs:
+        kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    prof = kg.profile(reset=True)
+    kg.set_profiling(False)
+    exp_ms, exp_launches = prof["expand"]
+    units = sum(s["work_units"] for s in stats)
+    items = sum(s["work_items"] for s in stats)
+    hits = sum(s["hits_central"] + s["hits_marginal"] for s in stats)
+    e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
+    alg_bytes = 4 * units + e_act + 2 * hits + 16 * items      # adjacency, level checks, writes, items
+    achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
+    peak, peak_kind = hbm_peak()
+    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2001_06770_b300", "csrc", "search_kernels.cu"),
+                                "rb").read()).hexdigest()[:12]
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == src_sha else None
+    total_ms = sum(v[0] for v in prof.values())
+    roof = {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "alg_bytes_per_launch": alg_bytes / max(exp_launches, 1),
+            "avg_launch_us": 1e3 * exp_ms / max(exp_launches, 1), "launches": exp_launches,
+            "share_of_device_time": exp_ms / total_ms if total_ms else None}
+    return roof, {k: v[0] for k, v in prof.items()}
+
+
+def base_line(args, ws, wl, value, t_step, steps):
+    return {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic"}
 
 
 def run(args):
@@ -176,11 +225,29 @@ def run(args):
     import paper_2001_06770_b300 as rpq
     import rpqgen
 
+    wl = WORKLOADS[args.workload]
     torch.cuda.set_device(local)
-    ds = rpqgen.make_dataset("medium")
-    qs = rpqgen.workload_queries("medium", ds)
-    nq = len(qs)
+    ds = rpqgen.make_dataset(wl["ds"])
+    qs = rpqgen.workload_queries(wl["queries"], ds)
+    if args.queries:
+        qs = qs[:args.queries]
     kg = rpq.KG.from_dataset(ds)
+    if wl["mode"] == "batch":
+        line = run_batch(args, ws, rank, local, wl, ds, qs, kg)
+    elif wl["mode"] == "serve":
+        line = run_serve(args, ws, rank, local, wl, ds, qs, kg)
+    else:
+        line = run_single(args, ws, rank, local, wl, ds, qs, kg)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    kg.close()
+    return 0
+
+
+def run_single(args, ws, rank, local, wl, ds, qs, kg):
+    import torch
+    import paper_2001_06770_b300 as rpq
+    nq = len(qs)
     stream = torch.cuda.ExternalStream(kg.slot_stream(0))
     # device-resident inputs and outputs
     kw_dev = [torch.tensor(list(q.central) + list(q.marginal), dtype=torch.int32, device="cuda") for q in qs]
@@ -195,8 +262,7 @@ def run(args):
                              out_dev[i].data_ptr(), nout_dev[i:].data_ptr())
 
     # per-query statistics (E_act etc.) and correctness of the device path
-    stats = []
-    host_res = []
+    stats, host_res = [], []
     for q in qs:
         r, st = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
         stats.append(st)
@@ -247,7 +313,7 @@ def run(args):
     h2d = 88 * nq                                  # parameter block with the keyword ids, per query
     d2h = sum(24 * q.k + 600 for q in qs)          # results + control block (600 B), per query
 
-    # batched: all 64 queries in one rpq_search_batch call (concurrent slots)
+    # batched: all queries in one rpq_search_batch call (concurrent slots)
     kg.search_batch(qs)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -255,32 +321,13 @@ def run(args):
     t_b = allmax(ws, time.perf_counter() - t0)
     batched = ws * nq * args.steps / t_b
 
-    # profiling pass: device time of each kernel class (events around launches)
-    kg.set_profiling(True)
-    for q in qs:
-        kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
-    prof = kg.profile(reset=True)
-    kg.set_profiling(False)
-    exp_ms, exp_launches = prof["expand"]
-    units = sum(s["work_units"] for s in stats)
-    items = sum(s["work_items"] for s in stats)
-    hits = sum(s["hits_central"] + s["hits_marginal"] for s in stats)
-    alg_bytes = 4 * units + e_act + 2 * hits + 16 * items      # adjacency, level checks, writes, items
-    achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
-    peak, peak_kind = hbm_peak()
-    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2001_06770_b300", "csrc", "search_kernels.cu"),
-                                "rb").read()).hexdigest()[:12]
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == src_sha else None
-
+    roof, kms = expand_roofline(kg, qs, stats)
     if rank != 0:
-        return 0
+        return None
     cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
-    total_ms = sum(v[0] for v in prof.values())
-    line = {
-        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
+    line = base_line(args, ws, wl, value, t_dev / args.steps, args.steps)
+    line.update({
+        "config": {"workload": wl["desc"], "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "gteps": e_act * ws * args.steps / t_dev / 1e9,
         "e_act_per_step": e_act,
@@ -288,19 +335,116 @@ def run(args):
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": alg_bytes / max(exp_launches, 1),
-                     "avg_launch_us": 1e3 * exp_ms / max(exp_launches, 1), "launches": exp_launches,
-                     "share_of_device_time": exp_ms / total_ms if total_ms else None},
-        "kernel_ms_per_step": {k: v[0] for k, v in prof.items()},
+        "roofline": roof,
+        "kernel_ms_per_step": kms,
         "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {cpu_n} of the 64 queries, serial C oracle, {cpu_s:.1f} s"},
+                         "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
         "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-    kg.close()
-    return 0
+    })
+    return line
+
+
+def run_batch(args, ws, rank, local, wl, ds, qs, kg):
+    """All queries in one rpq_search_batch call per step; a sample is also run
+    one at a time and must give identical results."""
+    nq = len(qs)
+    res0 = kg.search_batch(qs)
+    assert all(st == 0 for _, _, st in res0), "batch query failed"
+    sample = list(range(0, nq, max(1, nq // 128)))
+    t0 = time.perf_counter()
+    for i in sample:
+        r, _ = kg.search(qs[i].central, qs[i].marginal, qs[i].k, qs[i].max_depth, qs[i].gamma)
+        assert r.tobytes() == res0[i][0].tobytes(), f"batched result differs from one-at-a-time on query {i}"
+    one_qps = len(sample) / (time.perf_counter() - t0)
+    for _ in range(max(0, args.warmup - 1)):
+        kg.search_batch(qs)
+    clocks = Clocks(local)
+    barrier(ws)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = kg.search_batch(qs)
+    t = allmax(ws, time.perf_counter() - t0)
+    clk = clocks.stop()
+    value = ws * nq * args.steps / t
+    stats = [st for _, st, _ in out]
+    e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
+    sstats = [stats[i] for i in sample]
+    roof, kms = expand_roofline(kg, [qs[i] for i in sample], sstats)
+    if rank != 0:
+        return None
+    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    line = base_line(args, ws, wl, value, t / args.steps, args.steps)
+    line.update({
+        "config": {"workload": wl["desc"], "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
+                   "slots": 8, "l2": "inputs larger than L2 (3 GB adjacency)", "parallelism": f"replicas x{ws}"},
+        "gteps": e_act * ws * args.steps / t / 1e9,
+        "one_at_a_time_qps": one_qps,
+        "batched_vs_one_at_a_time": value / (ws * one_qps),
+        "equal_results_checked": len(sample),
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 88 * nq,
+                "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
+        "gpu_launches": sum(s["kernels"] for s in stats) * args.steps,
+        "roofline": roof, "kernel_ms_per_step_sample": kms,
+        "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
+        "clocks": clk,
+    })
+    return line
+
+
+def run_serve(args, ws, rank, local, wl, ds, qs, kg):
+    """Poisson arrival streams at several rates, served with continuous
+    batching under a 16 GB slot budget; each result must equal the query run
+    alone."""
+    import paper_2001_06770_b300 as rpq
+    import rpqgen
+    nq = len(qs)
+    srv = rpq.Server(kg, budget_bytes=16 << 30, max_slots=256)
+    info = srv.info()
+    sample = list(range(0, nq, max(1, nq // 64)))
+    alone = {i: kg.search(qs[i].central, qs[i].marginal, qs[i].k, qs[i].max_depth, qs[i].gamma)[0] for i in sample}
+    t0 = time.perf_counter()
+    for i in sample:
+        kg.search(qs[i].central, qs[i].marginal, qs[i].k, qs[i].max_depth, qs[i].gamma)
+    one_qps = len(sample) / (time.perf_counter() - t0)
+    srv.replay(qs[:2000], np.zeros(2000))                 # warm-up: graphs of every slot
+    rates = [5000.0, 10000.0, 20000.0, 50000.0]
+    per_rate = []
+    clocks = Clocks(local)
+    clocks.start()
+    for rate in rates:
+        arr = rpqgen.poisson_arrivals(nq, rate, seed=7)
+        res, lat, status, wall = srv.replay(qs, arr)
+        assert (status == 0).all()
+        for i in sample:
+            assert res[i].tobytes() == alone[i].tobytes(), f"served result differs from alone on query {i}"
+        per_rate.append({"rate_per_s": rate, "qps": nq / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall})
+    clk = clocks.stop()
+    srv.close()
+    if rank != 0:
+        return None
+    best = max(per_rate, key=lambda r: r["qps"])
+    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    line = base_line(args, ws, wl, ws * best["qps"], best["wall_s"], 1)
+    line.update({
+        "config": {"workload": wl["desc"], "queries": nq, "n": kg.n, "m2": kg.m2, "slots": info["slots"],
+                   "slot_bytes": info["slot_bytes"], "budget_bytes": 16 << 30, "l2": "inputs larger than L2",
+                   "parallelism": f"replicas x{ws}"},
+        "per_rate": per_rate,
+        "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"]},
+        "one_at_a_time_qps": one_qps,
+        "served_vs_one_at_a_time": best["qps"] / one_qps,
+        "equal_results_checked": len(sample),
+        "e2e": {"value": ws * best["qps"], "unit": "queries/s", "h2d_bytes_per_step": 88 * nq,
+                "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
+        "gpu_launches": None, "roofline": None,
+        "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
+        "clocks": clk,
+    })
+    return line
 
 
 def main():
@@ -310,6 +454,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rpq", choices=["rpq", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
+                    help="medium (default, the benchmark line), large, batched or served")
+    ap.add_argument("--queries", type=int, default=0, help="use only the first Q queries of the workload")
     ap.add_argument("--profile-only", type=int, default=0, metavar="Q",
                     help="load the workload, run its first Q queries once through rpq_search and exit "
                          "(a short command for ncu captures); prints no JSON line")
