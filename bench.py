@@ -464,16 +464,17 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_only:
-        return profile_only(args.profile_only)
+        return profile_only(args.profile_only, args.workload)
     return run(args)
 
 
-def profile_only(nq: int) -> int:
+def profile_only(nq: int, workload: str = "medium") -> int:
     import torch
     import paper_2001_06770_b300 as rpq
     import rpqgen
-    ds = rpqgen.make_dataset("medium")
-    qs = rpqgen.workload_queries("medium", ds)[:nq]
+    wl = WORKLOADS[workload]
+    ds = rpqgen.make_dataset(wl["ds"])
+    qs = rpqgen.workload_queries(wl["queries"], ds)[:nq]
     kg = rpq.KG.from_dataset(ds)
     for q in qs:
         kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
