@@ -90,16 +90,19 @@ RESULT_DTYPE = np.dtype([("node", np.int32), ("s_c", np.int32), ("s_m", np.int32
 
 
 def library_path() -> str:
-    return _build.LIB
+    """librpq.so of this package, or the file named by RPQ_LIBRARY (to compare
+    two builds of the library on the same inputs)."""
+    return os.environ.get("RPQ_LIBRARY") or _build.LIB
 
 
 def lib():
     """Load librpq.so, building it first when sources are newer."""
     global _lib
     if _lib is None:
-        if _build.stale():
+        path = library_path()
+        if path == _build.LIB and _build.stale():
             _build.build()
-        L = ctypes.CDLL(_build.LIB)
+        L = ctypes.CDLL(path)
         P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
         L.rpq_load_kg.argtypes = [ctypes.POINTER(KGDesc), ctypes.POINTER(P)]
         L.rpq_free_kg.argtypes = [P]
