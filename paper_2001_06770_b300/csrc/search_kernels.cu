@@ -277,29 +277,6 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         if (lane == 0 && word) Fc[widx] = 0;           // reset F for its next use
       }
     }
-    // every load of every round's node first (independent), then the logic,
-    // so a warp keeps kEnqRounds rounds of loads in flight
-    uint32_t cfw_r[kEnqRounds], vb_r[kEnqRounds], rb_r[kEnqRounds], re_r[kEnqRounds];
-    uint32_t h0_r[kEnqRounds], h1_r[kEnqRounds], ox_r[kEnqRounds];
-#pragma unroll
-    for (int r = 0; r < kEnqRounds; ++r) {
-      cfw_r[r] = vb_r[r] = rb_r[r] = re_r[r] = h0_r[r] = h1_r[r] = ox_r[r] = 0;
-      if (!has_r[r]) continue;
-      const uint32_t v = cand[r];
-      cfw_r[r] = ldx<P>(s.cf + (v >> 5));
-      vb_r[r] = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
-      rb_r[r] = g.row_ptr[v];
-      re_r[r] = g.row_ptr[v + 1];
-#pragma unroll
-      for (int j = 0; j < kMaxCols; ++j) {
-        const uint32_t h = j < nt ? uint32_t(ldx<P>(s.H + size_t(j) * s.hp + v)) : 0u;
-        if (j < 4) h0_r[r] |= h << (8 * j); else h1_r[r] |= h << (8 * (j - 4));
-      }
-      uint32_t o_lo = 0, o_hi = 0;
-      if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
-      if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
-      ox_r[r] = o_lo | (o_hi << 16);
-    }
     uint32_t my_items = 0, my_work = 0;
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
@@ -317,14 +294,25 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       bool expand = false, is_cg = false, stop_now = false;
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
-      const uint32_t cfw = cfw_r[r], vb = vb_r[r], rb = rb_r[r], re = re_r[r];
-      const uint32_t o_lo = ox_r[r] & 0xffffu, o_hi = ox_r[r] >> 16;
+      // every load of the node first (they are independent), then the logic
+      uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
+      uint32_t hv[kMaxCols];
+      if (has) {
+        cfw = ldx<P>(s.cf + (v >> 5));
+        vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
+        rb = g.row_ptr[v];
+        re = g.row_ptr[v + 1];
+#pragma unroll
+        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? ldx<P>(s.H + size_t(j) * s.hp + v) : 0u;
+        if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
+        if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
+      }
       if (has && !((cfw >> (v & 31u)) & 1u)) {
         uint32_t mx = 0;
 #pragma unroll
         for (int j = 0; j < kMaxCols; ++j) {
           if (j >= nt || !((vb >> j) & 1u)) continue;
-          const uint32_t h = ((j < 4 ? h0_r[r] : h1_r[r]) >> (8 * (j & 3))) & 0xffu;
+          const uint32_t h = hv[j];
           mx = h > mx ? h : mx;
           if (h == l) eq |= uint8_t(1u << j);
           else if (h < l) lt |= uint8_t(1u << j);
