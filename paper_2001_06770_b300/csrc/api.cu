@@ -94,6 +94,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.cf, nwords * 4 + 16);
   SA(d.stopl, n + 16);
   SA(d.items, sizeof(Item) * d.cap);
+  SA(d.imask, sizeof(uint16_t) * d.cap + 16);
   SA(d.cg, sizeof(uint32_t) * d.cap);
   const size_t tk = n / 32 + 4096;
   SA(d.topk[0], sizeof(uint32_t) * tk);

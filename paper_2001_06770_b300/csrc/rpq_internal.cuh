@@ -15,7 +15,8 @@
 //   F[2]     uint32[n/32]  Frontier Flag Array, double buffered by level
 //   cf       uint32[n/32]  Joining Flag Array (node stopped expanding)
 //   stopl    uint8[n]      level at which the cf bit was set
-//   items    Item[n]       expansion work list of the current level
+//   items    Item[n]       expansion work list of the current level (8 B each,
+//                          column masks in imask uint16[n])
 //   cg       uint32[n]     identified CGs, (level << 26) | node
 #pragma once
 #include <cstdint>
@@ -62,14 +63,12 @@ struct DevKG {
   const int32_t* kw_nodes;
 };
 
-// One expansion work item: a frontier node and its newly active segment.
-struct __align__(16) Item {
-  uint32_t node;
+// One expansion work item: the newly active segment of a frontier node.  The
+// item's column masks (columns with h == level in the low byte, h < level in
+// the high byte) are kept in a parallel uint16 array.
+struct __align__(8) Item {
   uint32_t seg_begin;  // first CSR entry of the segment
   uint32_t off;        // exclusive prefix of segment lengths (work units)
-  uint8_t eq;          // columns with h == level
-  uint8_t lt;          // columns with h < level
-  uint16_t pad;
 };
 
 // Query parameters as the kernels read them (device copy in the slot).
@@ -118,6 +117,7 @@ struct DevSlot {
   uint32_t* cf;
   uint8_t* stopl;
   Item* items;
+  uint16_t* imask;            // column masks of the items
   uint32_t* cg;
   uint32_t* topk[2];
   unsigned long long* rmask;  // recovery: per-column CG mask per node (kMaxCols * cap)

@@ -258,7 +258,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   const uint32_t kTile = sparse ? uint32_t(kEnqThreads) : uint32_t(kEnqThreads * kEnqRounds);
   uint32_t qcount = 0;
   for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
-    uint32_t it_node[kEnqRounds], it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
+    uint32_t it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
     // candidate node of each round: bitmap mode, word tile/32 + r*nwarp + warp
     // with lane = bit; queue mode, entry tile + r*blockDim + threadIdx
     uint32_t cand[kEnqRounds];
@@ -281,7 +281,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
       it_len[r] = 0;
-      it_node[r] = 0; it_seg[r] = 0; it_msk[r] = 0;
+      it_seg[r] = 0; it_msk[r] = 0;
       const bool has = has_r[r];
       if (!__any_sync(0xffffffffu, has)) continue;
       const uint32_t v = cand[r];
@@ -344,7 +344,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
                                : (l == 0 ? rb : ((indexed && l <= kLvxLevels) ? rb + o_lo : seg_lower(g.adj, rb, hi, l)));
         retain = hi < re;                              // an edge with a > l remains
         if (hi > lo) {
-          it_node[r] = v; it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
+          it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
           ++my_items;
           my_work += hi - lo;
         }
@@ -373,9 +373,10 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       for (int r = 0; r < kEnqRounds; ++r) {
         if (!it_len[r]) continue;
         Item it;
-        it.node = it_node[r]; it.seg_begin = it_seg[r]; it.off = off;
-        it.eq = uint8_t(it_msk[r]); it.lt = uint8_t(it_msk[r] >> 8); it.pad = 0;
+        it.seg_begin = it_seg[r];
+        it.off = off;
         s.items[idx] = it;
+        s.imask[idx] = uint16_t(it_msk[r]);
         const uint32_t last = off + it_len[r] - 1;     // warp tiles starting inside the item
         for (uint32_t t = (off + kWarpTile - 1) / kWarpTile; t <= last / kWarpTile; ++t) {
           if (t < s.tile_cap) s.tile_first[t] = idx; else atomicOr(&c->err, kErrOverflow);
@@ -411,13 +412,14 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 // gives the lane's item, so no barrier and no search are needed.  When the
 // kernel runs inside a graph WHILE node, block 0 ends the loop as the run stops.
 template <bool P>
-__device__ __forceinline__ void load_window(const Item* items, uint32_t n_items, uint32_t wb, uint32_t lane,
-                                            uint32_t& woff, uint32_t& wseg, uint32_t& wmsk) {
+__device__ __forceinline__ void load_window(const Item* items, const uint16_t* imask, uint32_t n_items, uint32_t wb,
+                                            uint32_t lane, uint32_t& woff, uint32_t& wseg, uint32_t& wmsk) {
   const uint32_t j = wb + lane;
   if (j < n_items) {
-    const uint4 raw = ldx<P>(reinterpret_cast<const uint4*>(items + j));
-    const Item it = *reinterpret_cast<const Item*>(&raw);
-    woff = it.off; wseg = it.seg_begin; wmsk = uint32_t(it.eq) | (uint32_t(it.lt) << 8);
+    const uint2 raw = ldx<P>(reinterpret_cast<const uint2*>(items + j));
+    wseg = raw.x;
+    woff = raw.y;
+    wmsk = ldx<P>(imask + j);
   } else {
     woff = 0xffffffffu; wseg = 0; wmsk = 0;
   }
@@ -475,7 +477,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
     const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
     uint32_t wb = ldx<P>(s.tile_first + t);
     uint32_t woff, wseg, wmsk;
-    load_window<P>(s.items, n_items, wb, lane, woff, wseg, wmsk);
+    load_window<P>(s.items, s.imask, n_items, wb, lane, woff, wseg, wmsk);
     uint32_t e_r[kExpRounds], m_r[kExpRounds];
     bool v_r[kExpRounds];
 #pragma unroll
@@ -488,7 +490,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
         const int hb = 31 - __clz(le);
         if (hb == 0) break;
         wb += uint32_t(hb);
-        load_window<P>(s.items, n_items, wb, lane, woff, wseg, wmsk);
+        load_window<P>(s.items, s.imask, n_items, wb, lane, woff, wseg, wmsk);
       }
       const uint32_t bit = (lane > 0 && woff < u0 + 32u) ? (1u << (woff - u0)) : 0u;
       const uint32_t starts = __reduce_or_sync(0xffffffffu, bit);
