@@ -132,6 +132,8 @@ def allmax(ws, x: float) -> float:
 def oracle_sample(ds, qs, n, act=None):
     """Serial oracle on the first n queries: (queries/s, seconds, n)."""
     import oracle
+    if n <= 0:
+        return None, 0.0, 0
     if act is None:
         act = oracle.dataset_activation(ds)
     t = time.perf_counter()
@@ -139,6 +141,18 @@ def oracle_sample(ds, qs, n, act=None):
         oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
     dt = time.perf_counter() - t
     return n / dt, dt, n
+
+
+def raks_cpu_sample(ds, qs, n):
+    """The paper's multi-core CPU search (OpenMP, all host cores) on the first
+    n queries: (queries/s, seconds, n, threads)."""
+    import raks_cpu
+    a = raks_cpu.activation(ds)
+    t = time.perf_counter()
+    for q in qs[:n]:
+        raks_cpu.search(ds, a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    dt = time.perf_counter() - t
+    return n / dt, dt, n, raks_cpu.threads()
 
 
 def run_reference(args):
@@ -325,6 +339,7 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
     if rank != 0:
         return None
     cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    mc = raks_cpu_sample(ds, qs, args.cpu_sample * 2) if args.cpu_sample else None
     line = base_line(args, ws, wl, value, t_dev / args.steps, args.steps)
     line.update({
         "config": {"workload": wl["desc"], "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
@@ -339,6 +354,9 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
         "kernel_ms_per_step": kms,
         "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
+        "raks_cpu": None if mc is None else {
+            "value": mc[0], "unit": "queries/s", "threads": mc[3], "kind": "paper's multi-core CPU search (OpenMP)",
+            "sample": f"first {mc[2]} of the {nq} queries, {mc[1]:.1f} s"},
         "clocks": clk,
     })
     return line
