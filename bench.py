@@ -230,7 +230,7 @@ def expand_roofline(kg, qs, stats):
 def base_line(args, ws, wl, value, t_step, steps):
     return {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u8", "data": "synthetic"}
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "tuning": args.tuning}
 
 
 def run(args):
@@ -246,6 +246,9 @@ def run(args):
     if args.queries:
         qs = qs[:args.queries]
     kg = rpq.KG.from_dataset(ds)
+    # work-split parameters picked by the library's autotuner on a sample
+    tuned = kg.autotune(qs[:16], repeats=2) if args.autotune else kg.tuning()
+    args.tuning = tuned
     if wl["mode"] == "batch":
         line = run_batch(args, ws, rank, local, wl, ds, qs, kg)
     elif wl["mode"] == "serve":
@@ -475,6 +478,7 @@ def main():
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
                     help="medium (default, the benchmark line), large, batched or served")
     ap.add_argument("--queries", type=int, default=0, help="use only the first Q queries of the workload")
+    ap.add_argument("--autotune", type=int, default=1, help="run the library's autotuner first (1) or not (0)")
     ap.add_argument("--profile-only", type=int, default=0, metavar="Q",
                     help="load the workload, run its first Q queries once through rpq_search and exit "
                          "(a short command for ncu captures); prints no JSON line")

@@ -221,6 +221,36 @@ int rpq_search_device(rpq_kg *kg, const int32_t *d_keywords, int32_t n_c, int32_
  * device-side error since the previous call. */
 int rpq_sync_device(rpq_kg *kg);
 
+/* ---------------------------------------------------------------- tuning */
+/* Work-split parameters of the search (they change timings, never results).
+ *   queue_div             a level's frontier is taken from a node queue while
+ *                         it holds at most n / queue_div nodes (at least 4096),
+ *                         otherwise from the frontier bit map (default 32)
+ *   next_queue_mult       the next level's queue is kept while the current
+ *                         level's work (CSR entries) is at most
+ *                         next_queue_mult x that limit (default 16)
+ *   batch_slots           concurrent search slots of rpq_search_batch (8)
+ *   flat_graph_max_depth  queries with max_depth up to this value replay a
+ *                         flat CUDA graph, deeper ones a graph with a WHILE
+ *                         node per run (12) */
+typedef struct {
+    int32_t queue_div;
+    int32_t next_queue_mult;
+    int32_t batch_slots;
+    int32_t flat_graph_max_depth;
+} rpq_tuning;
+
+int rpq_get_tuning(const rpq_kg *kg, rpq_tuning *out);
+/* Values < 1 are rejected (RPQ_EINVAL); captured CUDA graphs are rebuilt. */
+int rpq_set_tuning(rpq_kg *kg, const rpq_tuning *t);
+/* Autotuner: times the one-at-a-time search of the nq sample queries for each
+ * queue_div in {8, 32, 128} x next_queue_mult in {4, 16, 64}, then
+ * rpq_search_batch for batch_slots in {4, 8, 16}, keeps the fastest setting
+ * (the median of `repeats` timed passes after one warm-up pass decides) and
+ * returns it in *best (may be NULL).  Results are the same under every
+ * setting. */
+int rpq_autotune(rpq_kg *kg, const rpq_query *qs, int32_t nq, int32_t repeats, rpq_tuning *best);
+
 /* ------------------------------------------------------------- profiling */
 /* CUDA stream (a cudaStream_t) on which search slot `slot` runs its kernels;
  * slot 0 serves rpq_search, rpq_trace and rpq_search_device.  The slot is

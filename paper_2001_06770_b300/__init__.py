@@ -30,6 +30,7 @@ SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_se
            "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
            "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_info",
            "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
+           "rpq_get_tuning", "rpq_set_tuning", "rpq_autotune",
            "rpq_strerror", "rpq_last_error"]
 PROF_CLASSES = ["setup", "enqueue", "expand", "topk", "recover", "results"]
 
@@ -81,6 +82,14 @@ class Completion(ctypes.Structure):
                 ("res", ctypes.c_uint8 * (24 * MAX_K)), ("stats", Stats), ("latency_s", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("queue_div", ctypes.c_int32), ("next_queue_mult", ctypes.c_int32),
+                ("batch_slots", ctypes.c_int32), ("flat_graph_max_depth", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
@@ -123,6 +132,9 @@ def lib():
         L.rpq_server_poll.argtypes = [P, P, i32, P, i32]
         L.rpq_server_replay.argtypes = [P, P, P, i32, P, P, P, P, P]
         L.rpq_server_destroy.argtypes = [P]
+        L.rpq_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+        L.rpq_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+        L.rpq_autotune.argtypes = [P, P, i32, i32, ctypes.POINTER(Tuning)]
         L.rpq_strerror.argtypes = [ctypes.c_int]
         L.rpq_strerror.restype = ctypes.c_char_p
         L.rpq_last_error.restype = ctypes.c_char_p
@@ -274,6 +286,28 @@ class KG:
 
     def sync_device(self):
         _check(lib().rpq_sync_device(self._h))
+
+    def tuning(self):
+        t = Tuning()
+        _check(lib().rpq_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning(**{**self.tuning(), **kw})
+        _check(lib().rpq_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, queries, repeats: int = 3):
+        """Time the work-split settings on the sample queries and keep the
+        fastest (rpq_autotune); returns the chosen tuning."""
+        queries = list(queries)
+        keep = []
+        arr = (Query * len(queries))()
+        for i, q in enumerate(queries):
+            arr[i] = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+        t = Tuning()
+        _check(lib().rpq_autotune(self._h, ctypes.cast(arr, ctypes.c_void_p), len(queries), int(repeats),
+                                  ctypes.byref(t)))
+        return t.as_dict()
 
     def slot_stream(self, slot: int = 0) -> int:
         """Raw cudaStream_t of a search slot (for CUDA-event timing)."""

@@ -1,6 +1,7 @@
 // C ABI of librpq (include/rpq.h): validation, graph load, search slots,
 // CUDA graphs per query shape, batches over concurrent slots, tracing.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -46,14 +47,25 @@ int dev_err_to_status(uint32_t err) {
 // Graph form of a query: a flat graph launches L+1 level pairs per run
 // (levels after the run stopped return at once); a loop graph runs the level
 // pair in a WHILE node as often as needed.  On B300 one WHILE iteration costs
-// more than two early-exit launches, so the flat form is used up to
-// kFlatGraphMaxDepth (RPQ_GRAPH_LOOP=1 / 0 forces loops / flat graphs).
-constexpr int kFlatGraphMaxDepth = 12;
-
-static bool graph_loops(int L) {
+// more than two early-exit launches, so the flat form is used up to the
+// tuning's flat_graph_max_depth (default 12; RPQ_GRAPH_LOOP=1 / 0 forces
+// loops / flat graphs).
+static bool graph_loops(const rpq_kg* kg, int L) {
   static int v = -2;
   if (v == -2) { const char* e = getenv("RPQ_GRAPH_LOOP"); v = (e && *e) ? (*e == '0' ? 0 : 1) : -1; }
-  return v == -1 ? (L > kFlatGraphMaxDepth) : (v == 1);
+  return v == -1 ? (L > kg->tune.flat_graph_max_depth) : (v == 1);
+}
+
+// Slot parameters that follow the tuning.  Graphs captured with other values
+// are dropped (kernel parameters are baked into them).
+void apply_tuning(rpq_kg* kg, Slot* s) {
+  const size_t n = size_t(kg->dev.n), nwords = (n + 31) / 32;
+  const size_t div = size_t(std::max(1, kg->tune.queue_div));
+  s->d.fq_limit = uint32_t(std::min<size_t>(s->d.cap, std::max<size_t>(n / div, std::min<size_t>(4096, s->d.cap))));
+  (void)nwords;
+  s->d.fq_next_mult = uint32_t(std::max(1, kg->tune.next_queue_mult));
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
 }
 
 static bool use_graphs() {
@@ -104,9 +116,8 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
   d.tile_cap = uint32_t(uint64_t(kg->m2) / 128 + 2);
   SA(d.tile_first, sizeof(uint32_t) * d.tile_cap);
-  d.fq_limit = uint32_t(std::min<size_t>(d.cap, std::max<size_t>(nwords, 4096)));
-  SA(d.fq[0], sizeof(uint32_t) * d.fq_limit);
-  SA(d.fq[1], sizeof(uint32_t) * d.fq_limit);
+  SA(d.fq[0], sizeof(uint32_t) * d.cap);         // any queue limit up to n fits
+  SA(d.fq[1], sizeof(uint32_t) * d.cap);
   SA(d.ulist, sizeof(uint32_t) * d.cap);
   SA(d.vcl, sizeof(uint32_t) * d.cap);
   SA(d.sticky, 16);
@@ -133,6 +144,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
   if (rc != RPQ_OK) { destroy_slot(s); return rc; }
   d.qlog = nullptr;
   d.qcap = 0;
+  apply_tuning(kg, s);
   *out = s;
   return RPQ_OK;
 }
@@ -266,7 +278,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
   (void)n_c;
   // a loop graph depends only on whether the query has marginal keywords; a
   // flat graph also on L
-  const bool loops = !s->d.persistent && graph_loops(L);
+  const bool loops = !s->d.persistent && graph_loops(kg, L);
   const uint64_t key = loops ? uint64_t(n_m > 0 ? 1 : 0) : ((uint64_t(L) << 8) | uint64_t(n_m > 0 ? 3 : 2));
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
@@ -352,13 +364,10 @@ void empty_result(int32_t* n_out, rpq_stats* stats) {
   }
 }
 
-static int slot_count() {
-  static int v = 0;
-  if (!v) {
-    const char* e = getenv("RPQ_SLOTS");
-    v = (e && atoi(e) > 0) ? std::min(atoi(e), 256) : 8;
-  }
-  return v;
+static int slot_count(const rpq_kg* kg) {
+  const char* e = getenv("RPQ_SLOTS");
+  if (e && atoi(e) > 0) return std::min(atoi(e), 256);
+  return std::max(1, std::min(kg->tune.batch_slots, 256));
 }
 
 }  // namespace rpq
@@ -481,7 +490,7 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
                      int32_t* status, rpq_stats* stats) {
   if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
-  const int nslots = std::max(1, std::min<int>(slot_count(), nq));
+  const int nslots = std::max(1, std::min<int>(slot_count(kg), nq));
   std::vector<Slot*> slots(size_t(nslots), nullptr);
   for (int i = 0; i < nslots; ++i) {          // slots 1..nslots: slot 0 serves single searches
     const int rc = get_slot(kg, size_t(i) + 1, &slots[size_t(i)]);
@@ -636,6 +645,85 @@ int rpq_search_device(rpq_kg* kg, const int32_t* d_keywords, int32_t n_c, int32_
   if (rc != RPQ_OK) return rc;
   RPQ_CUDA(cudaMemcpyAsync(d_out, s->d.res, sizeof(rpq_result) * size_t(k), cudaMemcpyDeviceToDevice, s->st));
   RPQ_CUDA(cudaMemcpyAsync(d_n_out, s->d.n_res, sizeof(int32_t), cudaMemcpyDeviceToDevice, s->st));
+  return RPQ_OK;
+}
+
+int rpq_get_tuning(const rpq_kg* kg, rpq_tuning* out) {
+  if (!kg || !out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  *out = kg->tune;
+  return RPQ_OK;
+}
+
+int rpq_set_tuning(rpq_kg* kg, const rpq_tuning* t) {
+  if (!kg || !t) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  if (t->queue_div < 1 || t->next_queue_mult < 1 || t->batch_slots < 1 || t->flat_graph_max_depth < 0) {
+    set_error(RPQ_EINVAL, "tuning values must be positive");
+    return RPQ_EINVAL;
+  }
+  for (Slot* s : kg->slots) RPQ_CUDA(cudaStreamSynchronize(s->st));
+  kg->tune = *t;
+  for (Slot* s : kg->slots) apply_tuning(kg, s);
+  return RPQ_OK;
+}
+
+int rpq_autotune(rpq_kg* kg, const rpq_query* qs, int32_t nq, int32_t repeats, rpq_tuning* best) {
+  if (!kg || !qs || nq < 1 || repeats < 1) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
+  using Clock = std::chrono::steady_clock;
+  std::vector<rpq_result> out(size_t(RPQ_MAX_K) * size_t(nq));
+  std::vector<int32_t> n_out(static_cast<size_t>(nq)), status(static_cast<size_t>(nq));
+  int rc = RPQ_OK;
+  auto median = [](std::vector<double> v) { std::sort(v.begin(), v.end()); return v[v.size() / 2]; };
+  auto time_single = [&](double* sec) -> int {
+    std::vector<double> t;
+    for (int pass = 0; pass <= repeats; ++pass) {
+      const auto t0 = Clock::now();
+      for (int32_t i = 0; i < nq; ++i) {
+        int32_t nr = 0;
+        const int r = rpq_search(kg, &qs[i], out.data(), &nr, nullptr);
+        if (r != RPQ_OK && r != RPQ_EINVAL) return r;
+      }
+      if (pass > 0) t.push_back(std::chrono::duration<double>(Clock::now() - t0).count());
+    }
+    *sec = median(t);
+    return RPQ_OK;
+  };
+  auto time_batch = [&](double* sec) -> int {
+    std::vector<double> t;
+    for (int pass = 0; pass <= repeats; ++pass) {
+      const auto t0 = Clock::now();
+      const int r = rpq_search_batch(kg, qs, nq, out.data(), n_out.data(), status.data(), nullptr);
+      if (r != RPQ_OK) return r;
+      if (pass > 0) t.push_back(std::chrono::duration<double>(Clock::now() - t0).count());
+    }
+    *sec = median(t);
+    return RPQ_OK;
+  };
+  // one-at-a-time needs at most k records per query
+  for (int32_t i = 0; i < nq; ++i)
+    if (qs[i].k > RPQ_MAX_K) { set_error(RPQ_EINVAL, "k above RPQ_MAX_K"); return RPQ_EINVAL; }
+  rpq_tuning cur = kg->tune, bestt = kg->tune;
+  double best_s = 1e30;
+  for (int qd : {8, 32, 128}) {
+    for (int nm : {4, 16, 64}) {
+      cur.queue_div = qd;
+      cur.next_queue_mult = nm;
+      if ((rc = rpq_set_tuning(kg, &cur)) != RPQ_OK) return rc;
+      double sec = 0;
+      if ((rc = time_single(&sec)) != RPQ_OK) return rc;
+      if (sec < best_s) { best_s = sec; bestt = cur; }
+    }
+  }
+  cur = bestt;
+  best_s = 1e30;
+  for (int bs : {4, 8, 16}) {
+    cur.batch_slots = bs;
+    if ((rc = rpq_set_tuning(kg, &cur)) != RPQ_OK) return rc;
+    double sec = 0;
+    if ((rc = time_batch(&sec)) != RPQ_OK) return rc;
+    if (sec < best_s) { best_s = sec; bestt.batch_slots = bs; }
+  }
+  if ((rc = rpq_set_tuning(kg, &bestt)) != RPQ_OK) return rc;
+  if (best) *best = bestt;
   return RPQ_OK;
 }
 

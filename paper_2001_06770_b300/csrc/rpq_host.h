@@ -84,6 +84,7 @@ struct rpq_kg {
   std::vector<int64_t> kw_ptr;   // host copy of the postings offsets
   std::vector<rpq::Slot*> slots; // search slots, created on first use
   rpq::Prof* prof = nullptr;      // profiling mode when non-NULL
+  rpq_tuning tune{32, 16, 8, 12}; // work-split parameters (rpq_set_tuning / rpq_autotune)
 };
 
 namespace rpq {
@@ -98,4 +99,5 @@ int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty)
 int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv);      // asynchronous
 int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats);
 void empty_result(int32_t* n_out, rpq_stats* stats);
+void apply_tuning(rpq_kg* kg, Slot* s);   // slot parameters from kg->tune; drops captured graphs
 }  // namespace rpq

@@ -127,6 +127,7 @@ struct DevSlot {
   uint32_t tile_cap;
   uint32_t* fq[2];            // frontier queues (nodes of F), per level parity
   uint32_t fq_limit;          // queue used while it holds at most this many nodes
+  uint32_t fq_next_mult;      // next queue kept while a level's work <= fq_next_mult * fq_limit
   uint32_t hp;                // column pitch of H (H[j * hp + v])
   uint32_t* ulist;
   uint32_t* vcl;              // V_C pairs (g << 26 | node)

@@ -465,7 +465,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   // if this level's work is small; a large level would overflow it anyway and
   // its appends would contend on one counter.
   const uint32_t fq_use_next = ldx<P>(&c->fq_use[p ^ 1]);
-  const bool use_next = fq_use_next != 0 && n_work <= 16u * s.fq_limit;
+  const bool use_next = fq_use_next != 0 && uint64_t(n_work) <= uint64_t(s.fq_next_mult) * s.fq_limit;
   if (fq_use_next && !use_next && blockIdx.x == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
   const uint32_t lane = lane_id();
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
