@@ -208,3 +208,24 @@ def test_graph_without_edges():
         assert res["node"].tolist() == [0] and res["s_c"].tolist() == [0]
     finally:
         kg.close()
+
+
+@pytest.mark.parametrize("alpha", [0.2, 0.8])
+def test_alpha_sweep(alpha):
+    """Other values of the scaling parameter alpha (Eq. 1-2; Section 5.2 sweeps
+    it): activation levels and results still equal the oracle's."""
+    ds = rpqgen.make_dataset("small")
+    g = ds.graph
+    act = oracle.activation(g.row_ptr, g.col, g.label, g.n_labels, alpha, ds.abar)
+    kg = rpq.KG(g.row_ptr, g.col, g.label, g.n_labels, ds.kw_ptr, ds.kw_nodes, alpha, ds.abar)
+    try:
+        adj, amax = kg.export()
+        assert np.array_equal(amax, act.amax)
+        src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+        expect = (act.a.astype(np.uint32) << 26) | g.col.astype(np.uint32)
+        assert np.array_equal(adj, expect[np.lexsort((expect, src))])
+        for q in dataset_queries("small", ds, 5, seed=61):
+            orc = oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
+            trace_matches(kg.trace(q.central, q.marginal, q.k, q.max_depth, q.gamma), orc)
+    finally:
+        kg.close()
