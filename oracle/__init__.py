@@ -31,7 +31,7 @@ INF = 255
 # field ids of orc_get (keep in step with the enum in rpq_oracle.c)
 (F_STATUS, F_NRES, F_RES_NODE, F_RES_SC, F_RES_SM, F_RES_SR, F_QPTR, F_QNODES, F_LAST_LEVEL,
  F_LAST_EXPANDED, F_EACT, F_NEWHITS, F_CG_NODE, F_CG_SCORE, F_CG_LEVEL, F_NSEL, F_SEL, F_SEL_SC,
- F_VC_ALL, F_VC_KW, F_EC, F_MATCHED, F_MATCH_LEVEL, F_SM, F_RAN) = range(25)
+ F_VC_ALL, F_VC_KW, F_EC, F_MATCHED, F_MATCH_LEVEL, F_SM, F_RAN, F_VM, F_EM, F_PTC) = range(28)
 
 
 def build_lib(force: bool = False) -> str:
@@ -133,6 +133,9 @@ class SearchResult:
     matched: np.ndarray
     match_level: np.ndarray
     sel_sm: np.ndarray
+    vm: list               # G^m nodes per selected CG (empty unless matched)
+    em: list               # G^m CSR entries per selected CG
+    ptc: np.ndarray        # Definition 5 check per selected CG: 1 holds, 0 violated, -1 not an RPG
 
 
 def _get(L, h, field, r=0, g=0, dtype=np.int64):
@@ -202,7 +205,10 @@ def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int
             ec=[_get(L, h, F_EC, 0, g_) for g_ in range(nsel)],
             matched=_get(L, h, F_MATCHED, dtype=np.int32),
             match_level=_get(L, h, F_MATCH_LEVEL, dtype=np.int32),
-            sel_sm=_get(L, h, F_SM, dtype=np.int32))
+            sel_sm=_get(L, h, F_SM, dtype=np.int32),
+            vm=[_get(L, h, F_VM, 0, g_) for g_ in range(nsel)],
+            em=[_get(L, h, F_EM, 0, g_) for g_ in range(nsel)],
+            ptc=_get(L, h, F_PTC, dtype=np.int32))
     finally:
         L.orc_free(h)
     return res

@@ -13,7 +13,11 @@
  *                    Theorem 3, expansion Algorithm 1), recovering phase
  *                    (Algorithm 2, Lemma 3), the two runs of Fig. 3 (central
  *                    keywords -> top-w CGs, marginal keywords -> RPGs), the
- *                    scores of Eq. 4-6 and top-k selection (Definition 6).
+ *                    scores of Eq. 4-6 and top-k selection (Definition 6);
+ *                    result subgraphs G^c (V^c, E^c) and G^m = U SP(m_i, V_C)
+ *                    (Definition 5, recovered with the two changes to
+ *                    Algorithm 2 of Section 4.3) and the PTC check of
+ *                    Definition 5 on each RPG.
  *
  * Readings taken where the paper is silent or ambiguous (each also listed in
  * the design notes of the repository):
@@ -41,6 +45,14 @@
  *     max_i min_{v in V_C} h^M[v][i].  The run ends when every selected CG is
  *     matched, at level L, or when the frontier empties.
  *   - |M| = 0: the results are the top-k CGs with S^m = 0 and S^r = S^c.
+ *   - G^m of a matched CG: for each marginal keyword m_i the sweep starts at
+ *     the nodes of V_C whose marginal hit level equals min_{v in V_C} h^M[v][i]
+ *     and follows tight edges with the marginal run's stop levels.  Edges are
+ *     CSR entries n -> q (n expanded to q); V^m includes those start nodes.
+ *   - PTC check: the RPG is G^c U G^m as an undirected graph; marginal keyword
+ *     nodes are its nodes holding a marginal keyword; the two nodes must be
+ *     distinct and hold different marginal keywords (columns); a path "passes
+ *     through" V_C when any of its nodes, endpoints included, is in V_C.
  *   - gamma defaults to 0.5; RPGs are ordered by (S^r, central node id).
  *   - A central (marginal) keyword with no keyword node yields no result.
  */
@@ -193,6 +205,8 @@ typedef struct {
     vec *vc_all;             /* V^c per selected CG (sorted) */
     vec *vc_kw;              /* V_C per selected CG (sorted) */
     vec *ec;                 /* recovered CSR entries per selected CG (sorted) */
+    vec *vm, *em;            /* RPG part G^m per matched CG: nodes, CSR entries (sorted) */
+    int32_t *ptc;            /* Definition 5 check per selected CG: 1, 0, -1 = not an RPG */
     int32_t *matched;        /* marginal run: matched flag */
     int32_t *match_level;
     int32_t *s_m;
@@ -336,41 +350,151 @@ static void explore(const orc_graph *G, const int32_t *kws, int32_t nt, int32_t 
     R->e_act = eact;
 }
 
-/* Recovering phase for one CG (Algorithm 2 with Lemma 3's condition). */
-static void recover(const orc_graph *G, const run_state *R, int64_t vc, vec *nodes, vec *edges) {
+/* Backward sweep of Algorithm 2 for one keyword column j: from the start
+ * nodes, follow every edge n -> q with h_q = max(a_nq, h_n) + 1 (Lemma 3)
+ * whose source n was still expanding at level max(a_nq, h_n), down to the
+ * keyword nodes (h = 0).  Appends new nodes to `nodes` (innodes marks them)
+ * and the CSR entries n -> q of the recovered paths to `edges`. */
+static void sweep(const orc_graph *G, const run_state *R, int32_t j, const int64_t *starts, int64_t ns,
+                  uint8_t *innodes, vec *nodes, vec *edges) {
     const int32_t nt = R->nt, n = G->n;
-    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
-    uint8_t *innodes = (uint8_t *)calloc((size_t)n, 1);
-    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
-    vpush(nodes, vc); innodes[vc] = 1;
-    for (int32_t j = 0; j < nt; ++j) {
-        memset(seen, 0, (size_t)n);
-        int64_t qh = 0, qt = 0;
-        if (R->h[vc * nt + j] == 0) continue;        /* v_c holds the keyword itself */
-        queue[qt++] = vc; seen[vc] = 1;
-        while (qh < qt) {
-            int64_t q = queue[qh++];
-            int hq = R->h[q * nt + j];
-            for (int64_t t = G->tptr[q]; t < G->tptr[q + 1]; ++t) {      /* in-neighbours of q */
-                int64_t e = G->tent[t];                                  /* entry vn -> q */
-                int64_t vn = G->tsrc[t];
-                int hn = R->h[vn * nt + j];
-                if (hn == (int)INF) continue;
-                int lam = G->a[e] > hn ? G->a[e] : hn;
-                if (hq != lam + 1) continue;                             /* not a tight edge */
-                if (!(lam < R->stop[vn])) continue;                      /* n never expanded at lam */
-                vpush(edges, e);
-                if (!innodes[vn]) { innodes[vn] = 1; vpush(nodes, vn); }
-                if (hn != 0 && !seen[vn]) { seen[vn] = 1; queue[qt++] = vn; }
+    uint8_t *seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t qh = 0, qt = 0;
+    for (int64_t i = 0; i < ns; ++i) {
+        int64_t v = starts[i];
+        if (!innodes[v]) { innodes[v] = 1; vpush(nodes, v); }
+        if (!seen[v]) { seen[v] = 1; queue[qt++] = v; }
+    }
+    while (qh < qt) {
+        int64_t q = queue[qh++];
+        int hq = R->h[q * nt + j];
+        if (hq == 0 || hq == (int)INF) continue;                     /* a keyword node: path start */
+        for (int64_t t = G->tptr[q]; t < G->tptr[q + 1]; ++t) {      /* in-neighbours of q */
+            int64_t e = G->tent[t];                                  /* entry vn -> q */
+            int64_t vn = G->tsrc[t];
+            int hn = R->h[vn * nt + j];
+            if (hn == (int)INF) continue;
+            int lam = G->a[e] > hn ? G->a[e] : hn;
+            if (hq != lam + 1) continue;                             /* not a tight edge */
+            if (!(lam < R->stop[vn])) continue;                      /* n never expanded at lam */
+            vpush(edges, e);
+            if (!innodes[vn]) { innodes[vn] = 1; vpush(nodes, vn); }
+            if (!seen[vn]) { seen[vn] = 1; queue[qt++] = vn; }
+        }
+    }
+    free(seen); free(queue);
+}
+
+static void sort_unique(vec *x) {
+    qsort(x->v, (size_t)x->n, sizeof(int64_t), cmp_i64);
+    int64_t w = 0;
+    for (int64_t i = 0; i < x->n; ++i) if (i == 0 || x->v[i] != x->v[i - 1]) x->v[w++] = x->v[i];
+    x->n = w;
+}
+
+/* Recovering phase for one CG (Algorithm 2 with Lemma 3's condition): the
+ * union over central columns of all recovered shortest paths from the
+ * keyword nodes to v_c, i.e. V^c and E^c. */
+static void recover(const orc_graph *G, const run_state *R, int64_t vc, vec *nodes, vec *edges) {
+    uint8_t *innodes = (uint8_t *)calloc((size_t)(G->n > 0 ? G->n : 1), 1);
+    innodes[vc] = 1; vpush(nodes, vc);
+    for (int32_t j = 0; j < R->nt; ++j) sweep(G, R, j, &vc, 1, innodes, nodes, edges);
+    free(innodes);
+    sort_unique(nodes);
+    sort_unique(edges);                              /* an edge may serve several columns */
+}
+
+/* Recovering phase of an RPG (Section 4.3, the two changes to Algorithm 2):
+ * the sweep of marginal column i starts from the nodes of V_C with the
+ * smallest marginal hit level d_i = min_{v in V_C} h^M[v][i], so only the
+ * smallest-score paths ending in V_C are kept: G^m = U_i SP(m_i, V_C)
+ * (Definition 5).  The stop levels are those of the marginal run. */
+static void recover_marginal(const orc_graph *G, const run_state *Rm, const vec *vck, vec *nodes, vec *edges) {
+    uint8_t *innodes = (uint8_t *)calloc((size_t)(G->n > 0 ? G->n : 1), 1);
+    int64_t *starts = (int64_t *)malloc(sizeof(int64_t) * (size_t)(vck->n > 0 ? vck->n : 1));
+    for (int32_t i = 0; i < Rm->nt; ++i) {
+        int d = INF;
+        for (int64_t t = 0; t < vck->n; ++t) {
+            int hv = Rm->h[vck->v[t] * Rm->nt + i];
+            if (hv < d) d = hv;
+        }
+        if (d == (int)INF) continue;                 /* keyword i never reached V_C */
+        int64_t ns = 0;
+        for (int64_t t = 0; t < vck->n; ++t) if (Rm->h[vck->v[t] * Rm->nt + i] == d) starts[ns++] = vck->v[t];
+        sweep(G, Rm, i, starts, ns, innodes, nodes, edges);
+    }
+    free(innodes); free(starts);
+    sort_unique(nodes);
+    sort_unique(edges);
+}
+
+/* Pass Through Constraint of Definition 5, checked on a finished RPG
+ * G^r = G^c U G^m taken as an undirected graph.  A marginal keyword node is a
+ * node of V^r that holds a marginal keyword (h^M = 0 in that column).  With
+ * |M| >= 2 the constraint holds when two different such nodes x, y, holding
+ * different marginal keywords, are joined only through V_C: x or y lies in
+ * V_C, or y cannot be reached from x in G^r once the nodes of V_C are
+ * removed.  With |M| = 1 it holds when some marginal keyword node is
+ * connected to a node of V_C in G^r.  Returns 1 (holds) or 0 (violated). */
+static int ptc_holds(const orc_graph *G, const run_state *Rm, const vec *vr, const vec *er, const vec *vck) {
+    const int32_t n = G->n, nt = Rm->nt;
+    uint8_t *in_vc = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    uint8_t *reach = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t t = 0; t < vck->n; ++t) in_vc[vck->v[t]] = 1;
+    /* undirected adjacency of G^r: for each node of V^r the edges touching it */
+    int64_t *deg = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t *ends = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(er->n > 0 ? er->n : 1));
+    for (int64_t t = 0; t < er->n; ++t) {
+        int64_t e = er->v[t];
+        int64_t u = 0, lo = 0, hi = n;               /* row of entry e */
+        while (lo < hi) { int64_t mid = (lo + hi) / 2; if (G->row_ptr[mid + 1] <= e) lo = mid + 1; else hi = mid; }
+        u = lo;
+        ends[2 * t] = u; ends[2 * t + 1] = G->col[e];
+        deg[u + 1]++; deg[G->col[e] + 1]++;
+    }
+    for (int32_t v = 0; v < n; ++v) deg[v + 1] += deg[v];
+    int64_t *adj = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(er->n > 0 ? er->n : 1));
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+    memcpy(cur, deg, sizeof(int64_t) * ((size_t)n + 1));
+    for (int64_t t = 0; t < er->n; ++t) {
+        adj[cur[ends[2 * t]]++] = ends[2 * t + 1];
+        adj[cur[ends[2 * t + 1]]++] = ends[2 * t];
+    }
+    int holds = 0;
+    for (int64_t t = 0; t < vr->n && !holds; ++t) {
+        int64_t x = vr->v[t];
+        for (int32_t i = 0; i < nt && !holds; ++i) {
+            if (Rm->h[x * nt + i] != 0) continue;    /* x does not hold m_i */
+            /* BFS from x in G^r; with |M| >= 2 it may not enter V_C */
+            memset(reach, 0, (size_t)(n > 0 ? n : 1));
+            int64_t qh = 0, qt = 0;
+            reach[x] = 1; queue[qt++] = x;
+            int touches_vc = in_vc[x];
+            while (qh < qt && !(nt >= 2 && in_vc[x])) {
+                int64_t u = queue[qh++];
+                for (int64_t p = deg[u]; p < deg[u + 1]; ++p) {
+                    int64_t v = adj[p];
+                    if (reach[v]) continue;
+                    if (in_vc[v]) touches_vc = 1;
+                    if (nt >= 2 && in_vc[v]) continue;
+                    reach[v] = 1; queue[qt++] = v;
+                }
+            }
+            if (nt == 1) { holds = touches_vc; continue; }
+            for (int64_t s = 0; s < vr->n && !holds; ++s) {
+                int64_t y = vr->v[s];
+                if (y == x) continue;
+                for (int32_t jj = 0; jj < nt; ++jj) {
+                    if (jj == i || Rm->h[y * nt + jj] != 0) continue;
+                    if (in_vc[x] || in_vc[y] || !reach[y]) { holds = 1; break; }
+                }
             }
         }
     }
-    free(seen); free(innodes); free(queue);
-    qsort(nodes->v, (size_t)nodes->n, sizeof(int64_t), cmp_i64);
-    qsort(edges->v, (size_t)edges->n, sizeof(int64_t), cmp_i64);
-    int64_t w = 0;                                   /* dedupe edges (one per column) */
-    for (int64_t i = 0; i < edges->n; ++i) if (i == 0 || edges->v[i] != edges->v[i - 1]) edges->v[w++] = edges->v[i];
-    edges->n = w;
+    free(in_vc); free(reach); free(queue); free(deg); free(ends); free(adj); free(cur);
+    return holds;
 }
 
 /* ----------------------------------------------------------- public result */
@@ -463,6 +587,23 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
         /* Second run: marginal keywords -> RPGs. */
         if (n_m > 0 && !empty_m && S->n_sel > 0)
             explore(&G, marginal, n_m, max_depth, RUN_MARGINAL, w, &res->rm, S, &opt);
+        /* Recovering phase of the RPGs: G^m and the PTC check of each match. */
+        S->vm = (vec *)calloc((size_t)(S->n_sel > 0 ? S->n_sel : 1), sizeof(vec));
+        S->em = (vec *)calloc((size_t)(S->n_sel > 0 ? S->n_sel : 1), sizeof(vec));
+        S->ptc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->n_sel > 0 ? S->n_sel : 1));
+        for (int32_t g = 0; g < S->n_sel; ++g) {
+            S->ptc[g] = -1;
+            if (!S->matched[g]) continue;
+            recover_marginal(&G, &res->rm, &S->vc_kw[g], &S->vm[g], &S->em[g]);
+            vec vr = {0, 0, 0}, er = {0, 0, 0};
+            for (int64_t t = 0; t < S->vc_all[g].n; ++t) vpush(&vr, S->vc_all[g].v[t]);
+            for (int64_t t = 0; t < S->vm[g].n; ++t) vpush(&vr, S->vm[g].v[t]);
+            for (int64_t t = 0; t < S->ec[g].n; ++t) vpush(&er, S->ec[g].v[t]);
+            for (int64_t t = 0; t < S->em[g].n; ++t) vpush(&er, S->em[g].v[t]);
+            sort_unique(&vr); sort_unique(&er);
+            S->ptc[g] = ptc_holds(&G, &res->rm, &vr, &er, &S->vc_kw[g]);
+            free(vr.v); free(er.v);
+        }
     }
 
     /* Scoring (Eq. 6) and top-k (Definition 6). */
@@ -502,7 +643,7 @@ enum {
     F_STATUS = 0, F_NRES, F_RES_NODE, F_RES_SC, F_RES_SM, F_RES_SR,
     F_QPTR, F_QNODES, F_LAST_LEVEL, F_LAST_EXPANDED, F_EACT, F_NEWHITS,
     F_CG_NODE, F_CG_SCORE, F_CG_LEVEL, F_NSEL, F_SEL, F_SEL_SC, F_VC_ALL, F_VC_KW, F_EC,
-    F_MATCHED, F_MATCH_LEVEL, F_SM, F_RAN
+    F_MATCHED, F_MATCH_LEVEL, F_SM, F_RAN, F_VM, F_EM, F_PTC
 };
 
 static int64_t copy64(const int64_t *src, int64_t n, void *dst) { if (dst && n) memcpy(dst, src, sizeof(int64_t) * (size_t)n); return n; }
@@ -538,6 +679,9 @@ int64_t orc_get(void *handle, int32_t field, int32_t r, int32_t g, void *dst) {
     case F_MATCHED: return copy32(S->matched, S->n_sel, dst);
     case F_MATCH_LEVEL: return copy32(S->match_level, S->n_sel, dst);
     case F_SM: return copy32(S->s_m, S->n_sel, dst);
+    case F_VM: return (g < S->n_sel && S->vm) ? copy64(S->vm[g].v, S->vm[g].n, dst) : 0;
+    case F_EM: return (g < S->n_sel && S->em) ? copy64(S->em[g].v, S->em[g].n, dst) : 0;
+    case F_PTC: return S->ptc ? copy32(S->ptc, S->n_sel, dst) : 0;
     }
     return -1;
 }
@@ -562,8 +706,12 @@ void orc_free(void *handle) {
     if (!res) return;
     free_run(&res->rc); free_run(&res->rm);
     cg_state *S = &res->S;
-    for (int32_t g = 0; g < S->n_sel; ++g) { free(S->vc_all[g].v); free(S->vc_kw[g].v); free(S->ec[g].v); }
+    for (int32_t g = 0; g < S->n_sel; ++g) {
+        free(S->vc_all[g].v); free(S->vc_kw[g].v); free(S->ec[g].v);
+        if (S->vm) { free(S->vm[g].v); free(S->em[g].v); }
+    }
     free(S->sel); free(S->sel_sc); free(S->vc_all); free(S->vc_kw); free(S->ec);
+    free(S->vm); free(S->em); free(S->ptc);
     free(S->matched); free(S->match_level); free(S->s_m);
     free(res->res_node); free(res->res_sc); free(res->res_sm); free(res->res_sr);
     free(res);

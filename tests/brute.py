@@ -10,6 +10,10 @@ from a different formulation of the paper's definitions.
   simultaneous equations (Jacobi iteration), instead of the level loop.
 * ``prefix_optimal_nodes``: nodes on paths whose every prefix is shortest,
   by forward path enumeration (what Algorithm 2 recovers, Lemma 3).
+* ``recovered_paths``: the paths Algorithm 2 recovers (Lemma 3, the stop
+  guard, the RPG start nodes of Section 4.3), by forward path enumeration.
+* ``ptc_by_paths``: the Pass Through Constraint of Definition 5 by
+  enumerating every simple path between marginal keyword nodes.
 * ``small_graph``: random simple graphs of at most 20 nodes.
 """
 from __future__ import annotations
@@ -202,3 +206,79 @@ def prefix_optimal_nodes(g, a, sources, target, dist):
         if dist[s] == 0:
             dfs(s, 0, [s])
     return found
+
+
+def recovered_paths(g, a, dist, stop, sources, targets):
+    """Union of the simple paths from `sources` to `targets` along which every
+    step u -> v (CSR entry e) is an expansion that happened: u was reached
+    (dist[u] finite), lam = max(dist[u], a[e]) is below u's stop level and
+    v was first hit at lam + 1 (forward enumeration).  Returns the node set
+    and the set of (u, v) steps.  With `stop` None no node ever stopped."""
+    nbrs = [[(int(g.col[e]), int(a[e])) for e in range(g.row_ptr[u], g.row_ptr[u + 1])] for u in range(g.n)]
+    targets = set(int(t) for t in targets)
+    nodes, steps = set(), set()
+
+    def dfs(u, path):
+        if u in targets:
+            nodes.update(path)
+            steps.update(zip(path[:-1], path[1:]))
+            return
+        for v, av in nbrs[u]:
+            if v in path:
+                continue
+            lam = max(int(dist[u]), av)
+            if stop is not None and not lam < int(stop[u]):
+                continue
+            if int(dist[v]) != lam + 1:
+                continue
+            path.append(v)
+            dfs(v, path)
+            path.pop()
+
+    for s in sources:
+        if int(dist[s]) == 0:
+            dfs(int(s), [int(s)])
+    return nodes, steps
+
+
+def ptc_by_paths(n_m, pairs, vc, holders):
+    """Pass Through Constraint of Definition 5 by enumerating simple paths of
+    the undirected graph given by `pairs`.  `holders` maps each node holding
+    a marginal keyword to the set of marginal columns it holds; `vc` is V_C.
+    |M| >= 2: some two distinct holders of different columns are joined only
+    by paths with a node (endpoints included) in V_C.  |M| = 1: some holder
+    has a path to a node of V_C (or lies in V_C)."""
+    adj = {}
+    for u, v in pairs:
+        adj.setdefault(u, set()).add(v)
+        adj.setdefault(v, set()).add(u)
+    vc = set(vc)
+
+    def paths(x, y):
+        out = []
+
+        def dfs(u, path):
+            if u == y:
+                out.append(list(path))
+                return
+            for w in sorted(adj.get(u, ())):
+                if w not in path:
+                    path.append(w)
+                    dfs(w, path)
+                    path.pop()
+        dfs(x, [x])
+        return out
+
+    hs = sorted(holders)
+    if n_m == 1:
+        for x in hs:
+            if x in vc or any(paths(x, v) for v in vc):
+                return 1
+        return 0
+    for x in hs:
+        for y in hs:
+            if x == y or not any(i != j for i in holders[x] for j in holders[y]):
+                continue
+            if all(any(w in vc for w in p) for p in paths(x, y)):
+                return 1
+    return 0

@@ -348,3 +348,101 @@ def test_golden_recovery_stop_guard():
     for gi, pairs in enumerate(fx["ec_pairs"]):
         assert sorted([int(src[e]), int(g.col[e])] for e in r.ec[gi]) == sorted(pairs)
     assert result_rows(r) == fx["results"]
+
+
+# ------------------------------------------------------ result subgraphs
+def pairs_of(g, entries):
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    return sorted([int(src[e]), int(g.col[e])] for e in entries)
+
+
+def test_golden_subgraphs_and_ptc():
+    """Hand-derived RPGs: V^c/E^c, G^m (Section 4.3 start nodes, several start
+    nodes at an equal minimum) and the PTC check, held and violated."""
+    fx = json.load(open(os.path.join(GOLDEN, "search_subgraphs.json")))
+    for case in fx["cases"]:
+        g, a, kp, kn = golden_graph(case["n"], case["edges"], case["postings"])
+        r = run(g, a, kp, kn, case["central"], case["marginal"], case["k"], case["L"])
+        assert result_rows(r) == case["results"], case["name"]
+        assert r.vc_all[0].tolist() == case["vc_all"]
+        assert pairs_of(g, r.ec[0]) == case["ec_pairs"]
+        assert r.vc_kw[0].tolist() == case["vc_kw"]
+        assert r.vm[0].tolist() == case["vm"]
+        assert pairs_of(g, r.em[0]) == case["em_pairs"]
+        assert int(r.ptc[0]) == case["ptc"]
+
+
+def holders_of(sets, M, nodes):
+    out = {}
+    for i, kw in enumerate(M):
+        for v in sets[kw]:
+            if int(v) in nodes:
+                out.setdefault(int(v), set()).add(i)
+    return out
+
+
+def check_rpg_parts_brute(g, a, sets, r, M, L):
+    """G^m of each matched CG equals the union of the expansion paths from each
+    marginal keyword to the nodes of V_C at its smallest hit level, found by
+    forward path enumeration over the hit levels of an independent fixed point
+    (|M| >= 2, PTC stop) or of simple-path distances (|M| = 1, no stop); the
+    PTC flag equals simple-path enumeration of Definition 5.  Returns the
+    PTC flags of the matched CGs."""
+    rm = r.marginal
+    if rm is None:
+        return []
+    if len(M) >= 2:
+        h = brute.fixed_point(g, a, [sets[m] for m in M], rm.last_expanded, stop_rule=True)
+        fin = (h != INF).all(axis=1)
+        stop = np.where(fin, h.max(axis=1), 10 ** 9)
+    else:
+        h = brute.path_enum_distance(g, a, sets[M[0]], L)[:, None]
+        stop = None
+    flags = []
+    for gi in range(len(r.selected)):
+        if not r.matched[gi]:
+            assert len(r.vm[gi]) == 0 and int(r.ptc[gi]) == -1
+            continue
+        vck = [int(v) for v in r.vc_kw[gi]]
+        nodes, steps = set(), set()
+        for i, kw in enumerate(M):
+            d = min(int(h[v, i]) for v in vck)
+            assert d != INF
+            tg = [v for v in vck if int(h[v, i]) == d]
+            nd, st = brute.recovered_paths(g, a, h[:, i], stop, sets[kw], tg)
+            nodes |= nd | set(tg)
+            steps |= st
+        assert r.vm[gi].tolist() == sorted(nodes)
+        assert pairs_of(g, r.em[gi]) == sorted([u, v] for u, v in steps)
+        vr = set(r.vc_all[gi].tolist()) | nodes
+        er = [tuple(p) for p in pairs_of(g, r.ec[gi])] + sorted(steps)
+        flag = brute.ptc_by_paths(len(M), er, vck, holders_of(sets, M, vr))
+        assert int(r.ptc[gi]) == flag
+        flags.append(flag)
+    return flags
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_marginal_recovery_and_ptc_brute_force(seed):
+    rng, g, a, kp, kn, sets = random_case(seed, amax=3)
+    L = int(rng.integers(3, 9))
+    k = int(rng.integers(1, 4))
+    M = [2, 3] if seed % 2 == 0 else [2]
+    check_rpg_parts_brute(g, a, sets, run(g, a, kp, kn, [0, 1], M, k, L), M, L)
+
+
+def test_ptc_brute_force_with_violations():
+    """Seeds and shapes (|M| = 2, 3; few activation levels) where some RPGs
+    violate the PTC: both outcomes occur and agree with path enumeration."""
+    seen = set()
+    for seed in range(1000, 1100):
+        rng, g, a, kp, kn, sets = random_case(seed, amax=2)
+        M = [2, 3, 4] if seed % 2 else [2, 3]
+        seen.update(check_rpg_parts_brute(g, a, sets, run(g, a, kp, kn, [0, 1], M, 3, 6), M, 6))
+    assert seen == {0, 1}
+
+
+def test_no_marginal_keywords_gives_no_rpg_parts(tiny_ds, tiny_act):
+    r = oracle.search(tiny_ds, tiny_act.a, [124, 464], [], 5, 6)
+    assert len(r.selected) > 0
+    assert all(len(x) == 0 for x in r.vm) and (r.ptc == -1).all()
