@@ -40,6 +40,7 @@ extern "C" {
 #define RPQ_ECUDA     (-4)  /* a CUDA runtime call failed */
 #define RPQ_ELIMIT    (-5)  /* input beyond a documented size limit */
 #define RPQ_EINTERNAL (-6)  /* a device-side consistency check failed */
+#define RPQ_ESIZE     (-7)  /* a caller buffer is too small; the call reports the size needed */
 
 /* Documented limits of this build. */
 #define RPQ_MAX_NODES    (1 << 26)  /* node ids are packed in 26 bits */
@@ -203,6 +204,68 @@ typedef struct {
 /* Same search as rpq_search, also filling *trace (host buffers). */
 int rpq_trace(rpq_kg *kg, const rpq_query *q, rpq_result *out, int32_t *n_out, rpq_stats *stats,
               rpq_trace_buf *trace);
+
+/* ------------------------------------------------------ result subgraphs */
+/* rpq_search_subgraphs: the search of rpq_search (same results, ranks and
+ * scores) that also returns each result's subgraph and checks it.
+ *
+ * Per result r (ranked as in `out`) three node lists and two edge lists:
+ *   V^c  the CG's nodes: every node on a recovered shortest path from a
+ *        central keyword node to the central node (Definition 4; recovering
+ *        phase, Algorithm 2 with Lemma 3), the central node included;
+ *   V_C  the nodes of V^c that hold a central keyword;
+ *   V^m  the nodes of G^m = U_i SP(m_i, V_C) (Definition 5): for each
+ *        marginal keyword m_i, the recovered paths of the marginal run that
+ *        end at the nodes of V_C with the smallest hit level
+ *        min_{v in V_C} h^M[v][i] (the two changes to Algorithm 2 for RPGs,
+ *        Section 4.3), those end nodes included; empty when M is empty;
+ *   E^c, E^m  the edges of the same paths as (n, q) pairs of node ids, n
+ *        expanded to q (h_q = max(h_n, a_nq) + 1, and n had not stopped).
+ * Each list holds every element once, in no particular order.  ptc[r] is the
+ * Pass Through Constraint of Definition 5 checked on G^r = G^c U G^m taken
+ * as an undirected graph: 1 holds, 0 violated, -1 when M is empty.  With
+ * |M| >= 2 it holds when two distinct nodes of V^c U V^m holding different
+ * marginal keywords are joined only through V_C (one of them lies in V_C, or
+ * they are disconnected once the nodes of V_C are removed); with |M| = 1
+ * when a node holding the marginal keyword is connected to V_C.  The search
+ * itself never uses the check: it is a diagnostic of the heuristic.
+ *
+ * Layout of the caller-owned host buffers: list l (RPQ_SG_VC, RPQ_SG_VCKW,
+ * RPQ_SG_VM) of result r is nodes[node_off[3r+l] .. node_off[3r+l+1]); edge
+ * list l (RPQ_SG_EC, RPQ_SG_EM) is the pairs edges[2e], edges[2e+1] for e in
+ * [edge_off[2r+l], edge_off[2r+l+1]).  nodes_cap counts int32 entries of
+ * nodes, edges_cap counts pairs (edges holds 2 * edges_cap int32).  When
+ * nodes_total > nodes_cap or edges_total > edges_cap the call fills out,
+ * n_out, stats, the offsets, ptc and both totals, copies no list and returns
+ * RPQ_ESIZE: grow the buffers and call again (the search is deterministic).
+ * NULL list pointers with zero capacity are allowed for that size query.
+ *
+ * Synchronous, on search slot 0.  The device scratch for the lists is
+ * allocated on first use and grown when a query needs more; it is released
+ * with the graph.  Errors: RPQ_EINVAL, RPQ_ELIMIT, RPQ_ESIZE, RPQ_ENOMEM,
+ * RPQ_ECUDA, RPQ_EINTERNAL. */
+#define RPQ_SG_VC   0
+#define RPQ_SG_VCKW 1
+#define RPQ_SG_VM   2
+#define RPQ_SG_NODE_LISTS 3
+#define RPQ_SG_EC   0
+#define RPQ_SG_EM   1
+#define RPQ_SG_EDGE_LISTS 2
+
+typedef struct rpq_subgraphs {
+    int32_t *nodes;       /* in: host array of nodes_cap entries (may be NULL if 0) */
+    int64_t nodes_cap;
+    int32_t *edges;       /* in: host array of 2 * edges_cap entries */
+    int64_t edges_cap;
+    int64_t node_off[RPQ_MAX_K * RPQ_SG_NODE_LISTS + 1];   /* out */
+    int64_t edge_off[RPQ_MAX_K * RPQ_SG_EDGE_LISTS + 1];   /* out */
+    int32_t ptc[RPQ_MAX_K];                                 /* out, per result */
+    int64_t nodes_total;  /* out: entries needed in nodes */
+    int64_t edges_total;  /* out: pairs needed in edges */
+} rpq_subgraphs;
+
+int rpq_search_subgraphs(rpq_kg *kg, const rpq_query *q, rpq_result *out, int32_t *n_out, rpq_stats *stats,
+                         rpq_subgraphs *sg);
 
 /* ------------------------------------------------- device-resident inputs */
 /* rpq_search_device: the same search with the keyword ids already in device

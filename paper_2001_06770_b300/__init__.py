@@ -23,11 +23,12 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
 
-RPQ_OK, RPQ_EINVAL, RPQ_ENOMEM, RPQ_ETIMEOUT, RPQ_ECUDA, RPQ_ELIMIT, RPQ_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+RPQ_OK, RPQ_EINVAL, RPQ_ENOMEM, RPQ_ETIMEOUT, RPQ_ECUDA, RPQ_ELIMIT, RPQ_EINTERNAL, RPQ_ESIZE = \
+    0, -1, -2, -3, -4, -5, -6, -7
 MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
-           "rpq_trace", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
+           "rpq_trace", "rpq_search_subgraphs", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
            "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_info",
            "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
            "rpq_get_tuning", "rpq_set_tuning", "rpq_autotune",
@@ -94,6 +95,14 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
 
+class Subgraphs(ctypes.Structure):
+    """rpq_subgraphs of include/rpq.h."""
+    _fields_ = [("nodes", ctypes.c_void_p), ("nodes_cap", ctypes.c_int64),
+                ("edges", ctypes.c_void_p), ("edges_cap", ctypes.c_int64),
+                ("node_off", ctypes.c_int64 * (MAX_K * 3 + 1)), ("edge_off", ctypes.c_int64 * (MAX_K * 2 + 1)),
+                ("ptc", ctypes.c_int32 * MAX_K), ("nodes_total", ctypes.c_int64), ("edges_total", ctypes.c_int64)]
+
+
 RESULT_DTYPE = np.dtype([("node", np.int32), ("s_c", np.int32), ("s_m", np.int32), ("reserved", np.int32),
                          ("s_r", np.float64)])
 
@@ -120,6 +129,7 @@ def lib():
         L.rpq_search.argtypes = [P, ctypes.POINTER(Query), P, P, P]
         L.rpq_search_batch.argtypes = [P, P, i32, P, P, P, P]
         L.rpq_trace.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(TraceBuf)]
+        L.rpq_search_subgraphs.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(Subgraphs)]
         L.rpq_search_device.argtypes = [P, P, i32, i32, i32, i32, f64, P, P]
         L.rpq_sync_device.argtypes = [P]
         L.rpq_slot_stream.argtypes = [P, i32, ctypes.POINTER(P)]
@@ -276,6 +286,36 @@ class KG:
                     h_marginal=hm[:, :nm] if nm else None, frontiers_central=fr_c, frontiers_marginal=fr_m,
                     cgs=cgs[:tb.n_cgs].copy(), selected=np.array(tb.selected[:nsel], np.int64),
                     vc=[np.sort(vcs[(vcs >> 26) == g] & ((1 << 26) - 1)) for g in range(nsel)])
+
+    def search_subgraphs(self, central, marginal, k, max_depth, gamma=0.5, nodes_cap=1 << 16, edges_cap=1 << 16):
+        """Search one query and return (results, stats, subgraphs): one dict per
+        result with the node lists ``vc`` (V^c), ``vc_kw`` (V_C), ``vm`` (V^m),
+        the edge lists ``ec`` (E^c), ``em`` (E^m) as (n, q) rows, and ``ptc``
+        (1 holds, 0 violated, -1 without marginal keywords).  Lists are in no
+        particular order.  Buffers grow once when the library reports
+        RPQ_ESIZE."""
+        keep = []
+        q = _query(central, marginal, k, max_depth, gamma, keep)
+        out = np.zeros(max(int(k), 1), RESULT_DTYPE)
+        n_out = ctypes.c_int32()
+        st = Stats()
+        for _ in range(2):
+            nodes = np.empty(max(nodes_cap, 1), np.int32)
+            edges = np.empty((max(edges_cap, 1), 2), np.int32)
+            sg = Subgraphs(nodes.ctypes.data, nodes_cap, edges.ctypes.data, edges_cap)
+            rc = lib().rpq_search_subgraphs(self._h, ctypes.byref(q), _ptr(out), ctypes.byref(n_out),
+                                            ctypes.byref(st), ctypes.byref(sg))
+            if rc != RPQ_ESIZE:
+                break
+            nodes_cap, edges_cap = max(nodes_cap, sg.nodes_total), max(edges_cap, sg.edges_total)
+        _check(rc)
+        no, eo = list(sg.node_off), list(sg.edge_off)
+        subs = []
+        for r in range(n_out.value):
+            nl = [nodes[no[3 * r + i]:no[3 * r + i + 1]].copy() for i in range(3)]
+            el = [edges[eo[2 * r + i]:eo[2 * r + i + 1]].copy() for i in range(2)]
+            subs.append(dict(vc=nl[0], vc_kw=nl[1], vm=nl[2], ec=el[0], em=el[1], ptc=int(sg.ptc[r])))
+        return out[:n_out.value].copy(), st.as_dict(), subs
 
     def search_device(self, d_keywords: int, n_c: int, n_m: int, k: int, max_depth: int, gamma: float,
                       d_out: int, d_n_out: int):

@@ -13,17 +13,6 @@
 
 namespace rpq {
 
-int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
-void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof);
-void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
-                  cudaGraphConditionalHandle loop, bool in_graph);
-void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof);
-void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof);
-int kernels_fixed_per_query(int n_m);
-int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof);
-int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
-
 static thread_local std::string g_last_error;
 
 void set_error(int code, const char* fmt, ...) {
@@ -321,7 +310,7 @@ int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
   return RPQ_OK;
 }
 
-static void fill_stats(const Ctl& c, rpq_stats* st) {
+void fill_stats(const Ctl& c, rpq_stats* st) {
   if (!st) return;
   st->e_act_central = int64_t(c.e_act[0]);
   st->e_act_marginal = int64_t(c.e_act[1]);
@@ -385,6 +374,7 @@ const char* rpq_strerror(int code) {
     case RPQ_ECUDA: return "RPQ_ECUDA";
     case RPQ_ELIMIT: return "RPQ_ELIMIT";
     case RPQ_EINTERNAL: return "RPQ_EINTERNAL";
+    case RPQ_ESIZE: return "RPQ_ESIZE";
   }
   return "RPQ_E(unknown)";
 }
@@ -449,6 +439,7 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
 int rpq_free_kg(rpq_kg* kg) {
   if (!kg) return RPQ_OK;
   for (Slot* s : kg->slots) destroy_slot(s);
+  free_subgraph_scratch(kg);
   delete kg->prof;
   cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax); cudaFree(kg->d_lvx);
   cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);

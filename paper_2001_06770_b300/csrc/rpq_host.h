@@ -41,6 +41,8 @@ struct Slot {
 };
 
 // Optional per-launch timing with CUDA events (profiling mode, no graphs).
+struct SgScratch;   // subgraph.cu
+
 struct Prof {
   struct Rec { int cls; cudaEvent_t a, b; };
   std::vector<cudaEvent_t> pool;
@@ -85,6 +87,7 @@ struct rpq_kg {
   std::vector<rpq::Slot*> slots; // search slots, created on first use
   rpq::Prof* prof = nullptr;      // profiling mode when non-NULL
   rpq_tuning tune{32, 16, 8, 12}; // work-split parameters (rpq_set_tuning / rpq_autotune)
+  rpq::SgScratch* sg = nullptr;   // result-subgraph lists (rpq_search_subgraphs), grown on demand
 };
 
 namespace rpq {
@@ -100,4 +103,18 @@ int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv);      // asynchronous
 int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats);
 void empty_result(int32_t* n_out, rpq_stats* stats);
 void apply_tuning(rpq_kg* kg, Slot* s);   // slot parameters from kg->tune; drops captured graphs
+void fill_stats(const Ctl& c, rpq_stats* st);
+void free_subgraph_scratch(rpq_kg* kg);     // subgraph.cu
+
+// Kernel launch sequences (search_kernels.cu).
+int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
+void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof);
+void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
+                  cudaGraphConditionalHandle loop, bool in_graph);
+void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof);
+void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof);
+int kernels_fixed_per_query(int n_m);
+int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof);
+int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
 }  // namespace rpq

@@ -166,6 +166,35 @@ __device__ __forceinline__ uint32_t seg_at(const DevKG& g, uint32_t v, uint32_t 
   return seg_lower(g.adj, rb, re, x);
 }
 
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {
+  const uint32_t lane = lane_id();
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= uint32_t(o)) v += t;
+  }
+  return v;
+}
+
+// Exclusive block scan of one 64-bit value per thread; *total gets the sum.
+// s_warp must hold 33 entries.  Contains __syncthreads.
+static __device__ uint64_t block_excl_scan(uint64_t v, uint64_t* s_warp, uint64_t* total) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t incl = warp_incl_scan(v);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t t = lane < nw ? s_warp[lane] : 0;
+    const uint64_t ti = warp_incl_scan(t);
+    if (lane < nw) s_warp[lane] = ti - t;
+    if (lane == 31) s_warp[32] = ti;
+  }
+  __syncthreads();
+  const uint64_t r = s_warp[warp] + incl - v;
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
 int num_sms();
 
 }  // namespace rpq
