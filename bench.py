@@ -42,7 +42,16 @@ FALLBACK_HBM = 6400.0
 # DRAM bytes per expansion launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the kernel source with this SHA-1 prefix; the
 # value is reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"sha1": "b4f81834f7be", "bytes_per_launch": 5004117}
+NCU_TRAFFIC = {"sha1": "c6adda8a7d4f", "bytes_per_launch": 5004117}
+
+
+def expand_source_sha() -> str:
+    """SHA-1 prefix of the expansion section of search_kernels.cu (k_expand and
+    its helpers): the stored DRAM traffic is reported only while it is unchanged."""
+    text = open(os.path.join(ROOT, "paper_2001_06770_b300", "csrc", "search_kernels.cu")).read()
+    a = text.index("// ----------------------------------------------------------- level: expand")
+    b = text.index("// ------------------------------------------------------ persistent run kernel")
+    return hashlib.sha1(text[a:b].encode()).hexdigest()[:12]
 
 
 def hbm_peak():
@@ -215,9 +224,7 @@ def expand_roofline(kg, qs, stats):
     alg_bytes = 4 * units + e_act + 2 * hits + 16 * items      # adjacency, level checks, writes, items
     achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
-    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2001_06770_b300", "csrc", "search_kernels.cu"),
-                                "rb").read()).hexdigest()[:12]
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == src_sha else None
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == expand_source_sha() else None
     total_ms = sum(v[0] for v in prof.values())
     roof = {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -53,7 +53,7 @@ def _L():
         _lib.orc_activation.argtypes = [i32, i64, P, P, P, i32, f64, f64, P, P, P, P, P]
         _lib.orc_activation.restype = ctypes.c_int
         _lib.orc_search.argtypes = [i32, i64, P, P, P, i32, P, P, P, i32, P, i32, i32, i32, f64,
-                                    i32, i32, u64]
+                                    i32, i32, i32, i32, u64]
         _lib.orc_search.restype = P
         _lib.orc_get.argtypes = [P, i32, i32, i32, P]
         _lib.orc_get.restype = i64
@@ -169,9 +169,10 @@ def _run(L, h, r, n) -> RunTrace | None:
 
 def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int, gamma: float = 0.5,
            disable_stops: bool = False, exhaustive_marginal: bool = False, shuffle_seed: int = 0,
-           kw_ptr=None, kw_nodes=None) -> SearchResult:
+           kw_ptr=None, kw_nodes=None, w: int = 0, product: bool = False) -> SearchResult:
     """Run the oracle on one query.  ``ds_or_graph`` is an ``rpqgen.Dataset`` or
-    an ``rpqgen.Graph`` (then pass ``kw_ptr``/``kw_nodes``)."""
+    an ``rpqgen.Graph`` (then pass ``kw_ptr``/``kw_nodes``).  ``w`` is the CG
+    beam width (0: w = k), ``product`` selects the multiplicative S^r."""
     if hasattr(ds_or_graph, "graph"):
         g = ds_or_graph.graph
         kw_ptr, kw_nodes = ds_or_graph.kw_ptr, ds_or_graph.kw_nodes
@@ -188,8 +189,8 @@ def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int
     n = len(row_ptr) - 1
     h = L.orc_search(n, int(row_ptr[-1]), _p(row_ptr), _p(col), _p(a), len(kw_ptr) - 1, _p(kw_ptr),
                      _p(kw_nodes), _p(c), len(c), _p(m) if len(m) else None, len(m), int(k),
-                     int(max_depth), float(gamma), int(disable_stops), int(exhaustive_marginal),
-                     int(shuffle_seed))
+                     int(max_depth), float(gamma), int(w), int(bool(product)), int(disable_stops),
+                     int(exhaustive_marginal), int(shuffle_seed))
     try:
         nsel = _scalar(L, h, F_NSEL)
         res = SearchResult(

@@ -54,6 +54,14 @@
  *     distinct and hold different marginal keywords (columns); a path "passes
  *     through" V_C when any of its nodes, endpoints included, is in V_C.
  *   - gamma defaults to 0.5; RPGs are ordered by (S^r, central node id).
+ *   - Beam width w (top-w CGs, Section 3.4): w = k unless a larger w is
+ *     given.  The marginal run then also stops by Theorem 4, applied with
+ *     the smallest score a still unmatched CG g can reach,
+ *     combine(S^c(g), l+1) at Glevel l (the printed bound uses S^m of the
+ *     k-th RPG, which is <= l), and with ties decided by node id as in the
+ *     ranking, so the stop never changes the top-k.
+ *   - Multiplicative S^r (Section 3.3 allows one without a formula): the
+ *     product S^c * S^m; gamma is not used then.
  *   - A central (marginal) keyword with no keyword node yields no result.
  */
 #include <stdint.h>
@@ -265,16 +273,68 @@ static void identify(run_state *R, int mode, int32_t l, const int64_t *Q, int64_
     }
 }
 
-static int terminate_run(const run_state *R, int mode, const cg_state *S, int32_t w, const orc_options *opt) {
+/* Score of an RPG: Eq. 6 (weighted sum), or the multiplicative combination
+ * that Section 3.3 allows, read as the product S^c * S^m. */
+static double rpg_score(int64_t sc, int64_t sm, double gamma, int product) {
+    if (product) return (double)(sc * sm);
+    return gamma * (double)sc + (1.0 - gamma) * (double)sm;
+}
+
+typedef struct {
+    int32_t w, k;             /* beam width (CGs kept) and number of results */
+    double gamma;
+    int product;              /* multiplicative S^r */
+} score_params;
+
+/* Theorem 4 at Glevel l of the marginal run: with at least k RPGs matched,
+ * the search may stop when no CG still unmatched can give an RPG ranked
+ * before the k-th one.  An unmatched CG g matches at level l+1 or later, so
+ * its RPG scores at least combine(S^c(g), l+1) (both combinations grow with
+ * S^m); the k-th RPG (S^r_k, id_k) is compared with that bound on
+ * (score, node id), the ranking order. */
+static int theorem4_stop(const cg_state *S, int32_t l, const score_params *sp) {
+    int32_t nm = 0;
+    for (int32_t g = 0; g < S->n_sel; ++g) nm += S->matched[g] != 0;
+    if (nm < sp->k) return 0;
+    double *sr = (double *)malloc(sizeof(double) * (size_t)nm);
+    int64_t *id = (int64_t *)malloc(sizeof(int64_t) * (size_t)nm);
+    int32_t t = 0;
+    for (int32_t g = 0; g < S->n_sel; ++g)
+        if (S->matched[g]) { sr[t] = rpg_score(S->sel_sc[g], S->s_m[g], sp->gamma, sp->product); id[t] = S->sel[g]; ++t; }
+    /* k-th smallest (score, id): selection by repeated minimum */
+    double srk = 0.0; int64_t idk = -1;
+    uint8_t *used = (uint8_t *)calloc((size_t)nm, 1);
+    for (int32_t r = 0; r < sp->k; ++r) {
+        int32_t best = -1;
+        for (int32_t i = 0; i < nm; ++i) {
+            if (used[i]) continue;
+            if (best < 0 || sr[i] < sr[best] || (sr[i] == sr[best] && id[i] < id[best])) best = i;
+        }
+        used[best] = 1; srk = sr[best]; idk = id[best];
+    }
+    int stop = 1;
+    for (int32_t g = 0; g < S->n_sel && stop; ++g) {
+        if (S->matched[g]) continue;
+        double b = rpg_score(S->sel_sc[g], (int64_t)l + 1, sp->gamma, sp->product);
+        if (!(b > srk || (b == srk && S->sel[g] > idk))) stop = 0;
+    }
+    free(sr); free(id); free(used);
+    return stop;
+}
+
+static int terminate_run(const run_state *R, int mode, const cg_state *S, int32_t l, const score_params *sp,
+                         const orc_options *opt) {
     if (opt->disable_stops) return 0;
-    if (mode == RUN_CENTRAL) return R->cg_node.n >= w;             /* at least w CGs collected */
+    if (mode == RUN_CENTRAL) return R->cg_node.n >= sp->w;         /* at least w CGs collected */
     if (opt->exhaustive_marginal) return 0;
-    for (int32_t g = 0; g < S->n_sel; ++g) if (!S->matched[g]) return 0;
-    return 1;                                                        /* every selected CG matched */
+    int all = 1;
+    for (int32_t g = 0; g < S->n_sel; ++g) if (!S->matched[g]) all = 0;
+    if (all) return 1;                                              /* every selected CG matched */
+    return theorem4_stop(S, l, sp);
 }
 
 /* Exploration phase of one run (Section 4.2, Algorithm 1). */
-static void explore(const orc_graph *G, const int32_t *kws, int32_t nt, int32_t L, int mode, int32_t w,
+static void explore(const orc_graph *G, const int32_t *kws, int32_t nt, int32_t L, int mode, const score_params *sp,
                     run_state *R, cg_state *S, const orc_options *opt) {
     const int32_t n = G->n;
     R->nt = nt;
@@ -305,7 +365,7 @@ static void explore(const orc_graph *G, const int32_t *kws, int32_t nt, int32_t 
         vpush(&R->q_ptr, R->q_nodes.n);
         R->last_level = l;
         identify(R, mode, l, Q, nq, S, opt);
-        if (terminate_run(R, mode, S, w, opt) || l == L) break;
+        if (terminate_run(R, mode, S, l, sp, opt) || l == L) break;
 
         /* Expansion (Algorithm 1) at Glevel l. */
         if (opt->shuffle_seed) shuffle(Q, nq, &rs);
@@ -526,11 +586,11 @@ static int cmp_rec(const void *p, const void *q) {
 void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *col, const uint8_t *a,
                  int32_t n_kw, const int64_t *kw_ptr, const int32_t *kw_nodes,
                  const int32_t *central, int32_t n_c, const int32_t *marginal, int32_t n_m,
-                 int32_t k, int32_t max_depth, double gamma,
+                 int32_t k, int32_t max_depth, double gamma, int32_t w, int32_t product,
                  int32_t disable_stops, int32_t exhaustive_marginal, uint64_t shuffle_seed) {
     orc_result *res = (orc_result *)calloc(1, sizeof(orc_result));
     res->n_c = n_c; res->n_m = n_m;
-    if (n_c <= 0 || n_m < 0 || k <= 0 || max_depth < 0 || max_depth > 254) { res->status = -1; return res; }
+    if (n_c <= 0 || n_m < 0 || k <= 0 || max_depth < 0 || max_depth > 254 || (w != 0 && w < k)) { res->status = -1; return res; }
     for (int32_t j = 0; j < n_c; ++j) if (central[j] < 0 || central[j] >= n_kw) { res->status = -1; return res; }
     for (int32_t j = 0; j < n_m; ++j) if (marginal[j] < 0 || marginal[j] >= n_kw) { res->status = -1; return res; }
     orc_graph G = { n, m2, row_ptr, col, a, n_kw, kw_ptr, kw_nodes, NULL, NULL, NULL };
@@ -547,7 +607,9 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
         free(cur);
     }
     orc_options opt = { disable_stops, exhaustive_marginal, shuffle_seed };
-    const int32_t w = k;                             /* beam width w = k (Section 3.4) */
+    /* beam width: w = k unless given (Section 3.4 uses w = k; k <= w) */
+    const score_params sp = { w > 0 ? w : k, k, gamma, product };
+    const int32_t wb = sp.w;
     cg_state *S = &res->S;
 
     int empty_c = 0, empty_m = 0;
@@ -556,13 +618,13 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
 
     if (!empty_c) {
         /* First run: central keywords -> CGs. */
-        explore(&G, central, n_c, max_depth, RUN_CENTRAL, w, &res->rc, S, &opt);
+        explore(&G, central, n_c, max_depth, RUN_CENTRAL, &sp, &res->rc, S, &opt);
         /* Top-w CGs by (S^c, id). */
         int64_t ncg = res->rc.cg_node.n;
         int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(ncg > 0 ? ncg : 1));
         for (int64_t i = 0; i < ncg; ++i) { pairs[2 * i] = res->rc.cg_score.v[i]; pairs[2 * i + 1] = res->rc.cg_node.v[i]; }
         qsort(pairs, (size_t)ncg, 2 * sizeof(int64_t), cmp_cg);
-        S->n_sel = (int32_t)(ncg < w ? ncg : w);
+        S->n_sel = (int32_t)(ncg < wb ? ncg : wb);
         S->sel = (int64_t *)malloc(sizeof(int64_t) * (size_t)(S->n_sel > 0 ? S->n_sel : 1));
         S->sel_sc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(S->n_sel > 0 ? S->n_sel : 1));
         for (int32_t g = 0; g < S->n_sel; ++g) { S->sel[g] = pairs[2 * g + 1]; S->sel_sc[g] = pairs[2 * g]; }
@@ -586,7 +648,7 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
         }
         /* Second run: marginal keywords -> RPGs. */
         if (n_m > 0 && !empty_m && S->n_sel > 0)
-            explore(&G, marginal, n_m, max_depth, RUN_MARGINAL, w, &res->rm, S, &opt);
+            explore(&G, marginal, n_m, max_depth, RUN_MARGINAL, &sp, &res->rm, S, &opt);
         /* Recovering phase of the RPGs: G^m and the PTC check of each match. */
         S->vm = (vec *)calloc((size_t)(S->n_sel > 0 ? S->n_sel : 1), sizeof(vec));
         S->em = (vec *)calloc((size_t)(S->n_sel > 0 ? S->n_sel : 1), sizeof(vec));
@@ -616,7 +678,7 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
                 nr++;
             } else if (S->matched[g]) {
                 R[nr].node = S->sel[g]; R[nr].sc = (int32_t)S->sel_sc[g]; R[nr].sm = S->s_m[g];
-                R[nr].sr = gamma * (double)S->sel_sc[g] + (1.0 - gamma) * (double)S->s_m[g];
+                R[nr].sr = rpg_score(S->sel_sc[g], S->s_m[g], gamma, product);
                 nr++;
             }
         }

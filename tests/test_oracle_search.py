@@ -190,6 +190,12 @@ def test_brute_force_first_level(seed):
     rows = sorted((0.5 * smin + 0.5 * int(r.sel_sm[i]), first[i]) for i in range(k) if r.matched[i])
     assert [int(x) for x in r.nodes] == [v for _, v in rows]
     assert r.s_r.tolist() == [s for s, _ in rows]
+    # multiplicative S^r = S^c * S^m with the brute-force distances
+    rp = run(g, a, kp, kn, C, M, k, L, product=True)
+    dms = {vc: min(int(D[2][v]) for v in sorted(v for v in set(r.vc_kw[gi].tolist()))) for gi, vc in enumerate(first)}
+    rows = sorted((smin * dms[v], v) for v in first if dms[v] != INF)
+    assert [int(x) for x in rp.nodes] == [v for _, v in rows]
+    assert rp.s_r.tolist() == [float(s) for s, _ in rows]
 
 
 @pytest.mark.parametrize("seed", range(20))
@@ -305,6 +311,39 @@ def test_marginal_early_stop_equals_exhaustive(seed):
     r1 = run(g, a, kp, kn, [0, 1], [2, 3, 4], 3, 7)
     r2 = run(g, a, kp, kn, [0, 1], [2, 3, 4], 3, 7, exhaustive_marginal=True)
     assert result_rows(r1) == result_rows(r2)
+
+
+@pytest.mark.parametrize("product", [False, True])
+@pytest.mark.parametrize("gamma", [0.5, 0.3, 1.0, 0.0])
+def test_theorem4_beam_wider_than_k(gamma, product):
+    """k < w: the marginal run may stop by Theorem 4 before every selected CG
+    is matched; the top-k it returns equals (a) the top-k of an exhaustive
+    marginal run and (b) the first k results of the same query with k = w
+    (every matched RPG, ranked).  The stop does fire on some queries."""
+    fired = 0
+    for seed in range(60):
+        rng, g, a, kp, kn, sets = random_case(2000 + seed, amax=2)
+        C, M = [0, 1], ([2, 3] if seed % 3 else [2])
+        k, w = int(rng.integers(1, 3)), int(rng.integers(3, 6))
+        r = run(g, a, kp, kn, C, M, k, 7, gamma=gamma, w=w, product=product)
+        ex = run(g, a, kp, kn, C, M, k, 7, gamma=gamma, w=w, product=product, exhaustive_marginal=True)
+        full = run(g, a, kp, kn, C, M, w, 7, gamma=gamma, w=w, product=product, exhaustive_marginal=True)
+        assert result_rows(r) == result_rows(ex)
+        assert result_rows(r) == result_rows(full)[:k]
+        assert r.selected.tolist() == full.selected.tolist()        # the CG stage depends on w only
+        if r.marginal is not None and not r.matched.all() and r.marginal.last_level < ex.marginal.last_level:
+            fired += 1
+    assert fired > 0
+
+
+def test_product_score_ranks_by_product(tiny_ds, tiny_act):
+    """Multiplicative S^r = S^c * S^m: the same RPGs as Eq. 6, ranked by the
+    product of their integer scores, ties by node id."""
+    q = dict(central=[124, 464], marginal=[375, 63], k=10, max_depth=6)
+    add = oracle.search(tiny_ds, tiny_act.a, **q)
+    mul = oracle.search(tiny_ds, tiny_act.a, **q, product=True)
+    rows = sorted((int(c) * int(m), int(v), int(c), int(m)) for v, c, m in zip(add.nodes, add.s_c, add.s_m))
+    assert [[v, c, m, float(p)] for p, v, c, m in rows] == result_rows(mul)
 
 
 def test_duplicate_keywords_are_identical_columns(tiny_ds, tiny_act):
