@@ -106,9 +106,21 @@ int rpq_kg_info(const rpq_kg *kg, int32_t *n, int64_t *m2, int64_t *device_bytes
 /* One radial pattern query (Definition 1; Table 2 parameters).
  *   central, n_c   1 <= n_c <= RPQ_MAX_KEYWORDS keyword ids
  *   marginal, n_m  0 <= n_m <= RPQ_MAX_KEYWORDS keyword ids (NULL if 0)
- *   k              1 <= k <= RPQ_MAX_K; the CG beam width is w = k
+ *   k              1 <= k <= RPQ_MAX_K results
  *   max_depth      largest Glevel L, 0 <= L <= RPQ_MAX_LEVEL (paper: 20)
- *   gamma          weight of Eq. 6, 0 <= gamma <= 1 (default 0.5) */
+ *   gamma          weight of Eq. 6, 0 <= gamma <= 1 (default 0.5)
+ *   w              CG beam width (top-w CGs, Section 3.4), k <= w <= RPQ_MAX_K;
+ *                  0 means w = k, the paper's setting.  With w > k the
+ *                  marginal run also stops by Theorem 4 (applied exactly:
+ *                  it stops once no unmatched CG can still reach a score,
+ *                  node id pair ranked before the k-th RPG's, so the top-k
+ *                  equals that of a run to L)
+ *   score          RPQ_SCORE_SUM: S^r of Eq. 6; RPQ_SCORE_PRODUCT: the
+ *                  multiplicative combination Section 3.3 allows, taken as
+ *                  S^r = S^c * S^m (gamma unused).  With M empty S^r = S^c.
+ * A zero-initialised tail (w = 0, score = 0) gives the paper's defaults. */
+#define RPQ_SCORE_SUM     0
+#define RPQ_SCORE_PRODUCT 1
 typedef struct {
     const int32_t *central;
     int32_t n_c;
@@ -117,6 +129,8 @@ typedef struct {
     int32_t k;
     int32_t max_depth;
     double gamma;
+    int32_t w;
+    int32_t score;
 } rpq_query;
 
 /* One result: the central node of the RPG (or of the CG when M is empty) and

@@ -52,7 +52,10 @@ class KGDesc(ctypes.Structure):
 class Query(ctypes.Structure):
     _fields_ = [("central", ctypes.c_void_p), ("n_c", ctypes.c_int32), ("marginal", ctypes.c_void_p),
                 ("n_m", ctypes.c_int32), ("k", ctypes.c_int32), ("max_depth", ctypes.c_int32),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("w", ctypes.c_int32), ("score", ctypes.c_int32)]
+
+
+SCORE_SUM, SCORE_PRODUCT = 0, 1
 
 
 class Stats(ctypes.Structure):
@@ -177,13 +180,23 @@ class QuerySpec:
     k: int
     max_depth: int
     gamma: float = 0.5
+    w: int = 0
+    product: bool = False
 
 
-def _query(central, marginal, k, max_depth, gamma, keep):
+def _query(central, marginal, k, max_depth, gamma, keep, w=0, product=False):
     c = np.ascontiguousarray(central, np.int32)
     m = np.ascontiguousarray(marginal, np.int32)
     keep.extend([c, m])
-    return Query(_ptr(c), len(c), _ptr(m) if len(m) else None, len(m), int(k), int(max_depth), float(gamma))
+    return Query(_ptr(c), len(c), _ptr(m) if len(m) else None, len(m), int(k), int(max_depth), float(gamma),
+                 int(w), SCORE_PRODUCT if product else SCORE_SUM)
+
+
+def _query_of(q, keep):
+    """rpq_query of a query object (central, marginal, k, max_depth and
+    optional gamma, w, product attributes)."""
+    return _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep,
+                  getattr(q, "w", 0), getattr(q, "product", False))
 
 
 class KG:
@@ -230,9 +243,9 @@ class KG:
         _check(lib().rpq_kg_export(self._h, _ptr(adj), _ptr(amax)))
         return adj, amax
 
-    def search(self, central, marginal, k, max_depth, gamma=0.5):
+    def search(self, central, marginal, k, max_depth, gamma=0.5, w=0, product=False):
         keep = []
-        q = _query(central, marginal, k, max_depth, gamma, keep)
+        q = _query(central, marginal, k, max_depth, gamma, keep, w, product)
         out = np.zeros(max(int(k), 1), RESULT_DTYPE)
         n_out = ctypes.c_int32()
         st = Stats()
@@ -246,7 +259,7 @@ class KG:
         keep = []
         arr = (Query * max(len(queries), 1))()
         for i, qs in enumerate(queries):
-            arr[i] = _query(qs.central, qs.marginal, qs.k, qs.max_depth, getattr(qs, "gamma", 0.5), keep)
+            arr[i] = _query_of(qs, keep)
         ks = [int(q.k) for q in queries]
         base = np.concatenate([[0], np.cumsum(ks)]).astype(np.int64)
         out = np.zeros(max(int(base[-1]), 1), RESULT_DTYPE)
@@ -257,10 +270,10 @@ class KG:
                                       _ptr(n_out), _ptr(status), ctypes.cast(st, ctypes.c_void_p)))
         return [(out[base[i]:base[i] + n_out[i]].copy(), st[i].as_dict(), int(status[i])) for i in range(len(queries))]
 
-    def trace(self, central, marginal, k, max_depth, gamma=0.5, frontier_cap=None):
+    def trace(self, central, marginal, k, max_depth, gamma=0.5, frontier_cap=None, w=0, product=False):
         """Search one query and return its intermediate state for inspection."""
         keep = []
-        q = _query(central, marginal, k, max_depth, gamma, keep)
+        q = _query(central, marginal, k, max_depth, gamma, keep, w, product)
         nc, nm = len(central), len(marginal)
         cap = frontier_cap or self.n * (max_depth + 1)
         hc = np.empty((self.n, nc), np.uint8)
@@ -287,7 +300,8 @@ class KG:
                     cgs=cgs[:tb.n_cgs].copy(), selected=np.array(tb.selected[:nsel], np.int64),
                     vc=[np.sort(vcs[(vcs >> 26) == g] & ((1 << 26) - 1)) for g in range(nsel)])
 
-    def search_subgraphs(self, central, marginal, k, max_depth, gamma=0.5, nodes_cap=1 << 16, edges_cap=1 << 16):
+    def search_subgraphs(self, central, marginal, k, max_depth, gamma=0.5, nodes_cap=1 << 16, edges_cap=1 << 16,
+                         w=0, product=False):
         """Search one query and return (results, stats, subgraphs): one dict per
         result with the node lists ``vc`` (V^c), ``vc_kw`` (V_C), ``vm`` (V^m),
         the edge lists ``ec`` (E^c), ``em`` (E^m) as (n, q) rows, and ``ptc``
@@ -295,7 +309,7 @@ class KG:
         particular order.  Buffers grow once when the library reports
         RPQ_ESIZE."""
         keep = []
-        q = _query(central, marginal, k, max_depth, gamma, keep)
+        q = _query(central, marginal, k, max_depth, gamma, keep, w, product)
         out = np.zeros(max(int(k), 1), RESULT_DTYPE)
         n_out = ctypes.c_int32()
         st = Stats()
@@ -343,7 +357,7 @@ class KG:
         keep = []
         arr = (Query * len(queries))()
         for i, q in enumerate(queries):
-            arr[i] = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+            arr[i] = _query_of(q, keep)
         t = Tuning()
         _check(lib().rpq_autotune(self._h, ctypes.cast(arr, ctypes.c_void_p), len(queries), int(repeats),
                                   ctypes.byref(t)))
@@ -380,7 +394,7 @@ class Server:
 
     def submit(self, q, tag: int):
         keep = []
-        qq = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+        qq = _query_of(q, keep)
         _check(lib().rpq_server_submit(self._h, ctypes.byref(qq), ctypes.c_uint64(tag)))
 
     def poll(self, wait: bool = False, max_done: int = 256):
@@ -404,7 +418,7 @@ class Server:
         keep = []
         arr = (Query * max(nq, 1))()
         for i, q in enumerate(queries):
-            arr[i] = _query(q.central, q.marginal, q.k, q.max_depth, getattr(q, "gamma", 0.5), keep)
+            arr[i] = _query_of(q, keep)
         t = np.ascontiguousarray(arrival_s, np.float64)
         lat = np.zeros(max(nq, 1), np.float64)
         status = np.zeros(max(nq, 1), np.int32)

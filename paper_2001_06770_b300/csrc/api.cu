@@ -178,6 +178,14 @@ int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty)
     return RPQ_EINVAL;
   }
   if (!(q->gamma >= 0.0 && q->gamma <= 1.0)) { set_error(RPQ_EINVAL, "need 0 <= gamma <= 1"); return RPQ_EINVAL; }
+  if (q->w != 0 && (q->w < q->k || q->w > kMaxK)) {
+    set_error(RPQ_EINVAL, "need w = 0 or k <= w <= %d (got k %d, w %d)", kMaxK, q->k, q->w);
+    return RPQ_EINVAL;
+  }
+  if (q->score != RPQ_SCORE_SUM && q->score != RPQ_SCORE_PRODUCT) {
+    set_error(RPQ_EINVAL, "unknown score combination %d", q->score);
+    return RPQ_EINVAL;
+  }
   memset(qv, 0, sizeof(*qv));
   *empty = false;
   for (int i = 0; i < q->n_c + q->n_m; ++i) {
@@ -190,6 +198,8 @@ int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty)
     qv->kw[i] = kw;
   }
   qv->n_c = q->n_c; qv->n_m = q->n_m; qv->k = q->k; qv->L = q->max_depth; qv->gamma = q->gamma;
+  qv->w = q->w ? q->w : q->k;
+  qv->product = q->score == RPQ_SCORE_PRODUCT;
   return RPQ_OK;
 }
 
@@ -629,7 +639,7 @@ int rpq_search_device(rpq_kg* kg, const int32_t* d_keywords, int32_t n_c, int32_
   if (rc != RPQ_OK) return rc;
   QueryDev qv;
   memset(&qv, 0, sizeof(qv));
-  qv.n_c = n_c; qv.n_m = n_m; qv.k = k; qv.L = max_depth; qv.gamma = gamma;
+  qv.n_c = n_c; qv.n_m = n_m; qv.k = k; qv.L = max_depth; qv.gamma = gamma; qv.w = k;
   rc = launch_query_setup(s->d, qv, d_keywords, s->st);
   if (rc != RPQ_OK) { set_error(RPQ_ECUDA, "launch failed"); return rc; }
   rc = enqueue_body(kg, s, n_c, n_m, max_depth);

@@ -76,6 +76,8 @@ struct QueryDev {
   int32_t kw[2 * kMaxCols];  // central ids then marginal ids
   int32_t n_c, n_m, k, L;
   double gamma;
+  int32_t w;                 // CG beam width, k <= w <= kMaxK
+  int32_t product;           // multiplicative S^r = S^c * S^m
 };
 
 // Control block of one slot, read and updated by the kernels of a search.
@@ -86,6 +88,7 @@ struct Ctl {
   int32_t last_expanded;       // last level with an expansion (-1: none)
   uint32_t nq[2];              // |Q_l| per level parity
   uint32_t n_matched;          // selected CGs matched so far (marginal run)
+  uint32_t rpg_stop;           // Theorem 4 ended the marginal run (w > k)
   uint32_t qlog_n;             // entries of the frontier log (trace mode)
   uint32_t ncg;                // CGs identified (central run)
   uint32_t err;                // DevErr bits

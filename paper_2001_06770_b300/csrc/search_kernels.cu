@@ -165,6 +165,44 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
   }
 }
 
+// ------------------------------------------------------------- RPG scores
+// S^r of Eq. 6, or the multiplicative combination S^c * S^m.  Explicit
+// round-to-nearest products and sum (no fused multiply-add), the same
+// operations as a plain double evaluation of the formula.
+__device__ __forceinline__ double rpg_score(const QueryDev& q, uint32_t sc, uint32_t sm) {
+  if (q.product) return double(sc * sm);
+  return __dadd_rn(__dmul_rn(q.gamma, double(sc)), __dmul_rn(1.0 - q.gamma, double(sm)));
+}
+
+// Theorem 4 at Glevel l of the marginal run (called with k <= matched < nsel):
+// a CG still unmatched matches at level l+1 or later, so its RPG scores at
+// least rpg_score(S^c, l+1); the run may stop when every such bound ranks
+// after the k-th matched RPG on (score, node id), the ranking order.
+__device__ bool theorem4_stop(const Ctl* c, const QueryDev& q, uint32_t nsel, uint32_t l) {
+  unsigned long long used = 0;
+  double srk = 0.0;
+  int32_t idk = -1;
+  for (int r = 0; r < q.k; ++r) {                         // k-th smallest by repeated minimum
+    int best = -1;
+    double bs = 0.0;
+    for (uint32_t gi = 0; gi < nsel; ++gi) {
+      if (!c->matched[gi] || ((used >> gi) & 1ull)) continue;
+      const double v = rpg_score(q, c->sel_sc[gi], c->sm[gi]);
+      if (best < 0 || v < bs || (v == bs && c->sel[gi] < c->sel[best])) { best = int(gi); bs = v; }
+    }
+    if (best < 0) return false;
+    used |= 1ull << best;
+    srk = bs;
+    idk = c->sel[best];
+  }
+  for (uint32_t gi = 0; gi < nsel; ++gi) {
+    if (c->matched[gi]) continue;
+    const double b = rpg_score(q, c->sel_sc[gi], l + 1);
+    if (!(b > srk || (b == srk && c->sel[gi] > idk))) return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------- level: enqueue
 // Frontier enqueue (Section 4.2.2): every node of F_l is taken and its flag
 // cleared - from the frontier queue when it is short (work proportional to
@@ -212,6 +250,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         nm += c->matched[gi];
       }
       c->n_matched = nm;
+      if (nm < nsel && nm >= uint32_t(q.k)) c->rpg_stop = theorem4_stop(c, q, nsel, l) ? 1u : 0u;
     }
   }
 
@@ -407,7 +446,8 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   const uint32_t n_items = uint32_t(wk >> kWorkBits);
   const uint32_t n_work = uint32_t(wk & kWorkMask);
   const uint32_t nq = ldx<P>(&c->nq[p]);
-  const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.k)) : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel));
+  const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.w))
+                             : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel) || ldx<P>(&c->rpg_stop));
   const bool stop = (nq == 0) || term || (l >= uint32_t(q.L));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->level = l;
@@ -588,7 +628,7 @@ k_run(DevKG g, DevSlot s, int run) {
 __global__ void __launch_bounds__(kTopkThreads)
 k_topk_pass(DevSlot s, int pass) {
   Ctl* c = s.ctl;
-  const uint32_t K = uint32_t(s.q->k);
+  const uint32_t K = uint32_t(s.q->w);                   // beam width w
   const uint32_t* src = pass == 0 ? s.cg : s.topk[(pass - 1) & 1];
   const uint32_t n_in = pass == 0 ? c->ncg : c->topk_n[(pass - 1) & 1];
   uint32_t* dst = s.topk[pass & 1];
@@ -629,7 +669,7 @@ k_topk_pass(DevSlot s, int pass) {
 __global__ void k_select(DevSlot s, int last_pass) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Ctl* c = s.ctl;
-  const uint32_t K = uint32_t(s.q->k);
+  const uint32_t K = uint32_t(s.q->w);
   const uint32_t* src = s.topk[last_pass & 1];
   const uint32_t n = min(c->topk_n[last_pass & 1], K);
   uint32_t ns = 0;
@@ -761,8 +801,8 @@ __global__ void k_recover_vc(DevSlot s) {
 }
 
 // --------------------------------------------------------------- results
-// Eq. 6 scores and the top-k by (S^r, node id).  With M empty the results
-// are the selected CGs with S^m = 0 and S^r = S^c.
+// Eq. 6 (or product) scores and the top-k by (S^r, node id).  With M empty
+// the results are the selected CGs with S^m = 0 and S^r = S^c.
 __global__ void k_results(DevSlot s) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
@@ -777,7 +817,7 @@ __global__ void k_results(DevSlot s) {
       if (q.n_m == 0) { s_ok[gi] = 1; s_sr[gi] = double(c->sel_sc[gi]); }
       else if (c->matched[gi]) {
         s_ok[gi] = 1;
-        s_sr[gi] = q.gamma * double(c->sel_sc[gi]) + (1.0 - q.gamma) * double(c->sm[gi]);
+        s_sr[gi] = rpg_score(q, c->sel_sc[gi], c->sm[gi]);
       }
     }
   }

@@ -253,6 +253,8 @@ class Query:
     k: int
     max_depth: int
     gamma: float = 0.5
+    w: int = 0                # CG beam width (0: w = k)
+    product: bool = False     # multiplicative S^r
 
 
 def _rng(seed: int, stream: int) -> np.random.Generator:

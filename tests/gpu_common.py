@@ -50,7 +50,8 @@ def trace_matches(tr, orc, check_stats=True):
 
 
 def oracle_query(ds, act, q):
-    return oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
+    return oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma,
+                         w=getattr(q, "w", 0), product=getattr(q, "product", False))
 
 
 def dataset_queries(name, ds, n, seed=3):
