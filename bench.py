@@ -196,6 +196,8 @@ def run_reference(args):
 
 WORKLOADS = {
     "medium": dict(ds="medium", queries="medium", mode="single", desc=WORKLOAD),
+    "tiny": dict(ds="tiny", queries="tiny", mode="single",
+                 desc="tiny: R-MAT 2^14 nodes, one RPQ (smoke and multi-process checks, not a bench line)"),
     "large": dict(ds="large", queries="large", mode="single",
                   desc="large: Chung-Lu (exponent 2.1) 5e7 nodes, 4e8 sampled edges, symmetric int32 CSR; "
                        "256 RPQs one at a time, |C| = |M| = 3, ranks 100-20000, k=20, L=8"),
