@@ -222,8 +222,9 @@ def expand_roofline(kg, qs, stats):
     units = sum(s["work_units"] for s in stats)
     items = sum(s["work_items"] for s in stats)
     hits = sum(s["hits_central"] + s["hits_marginal"] for s in stats)
-    e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
-    alg_bytes = 4 * units + e_act + 2 * hits + 16 * items      # adjacency, level checks, writes, items
+    # activations the expansion kernel executed (E_act less the skipped final marginal levels)
+    e_act = sum(s["e_act_central"] + s["e_act_marginal"] - s["e_act_skipped"] for s in stats)
+    alg_bytes = 4 * units + e_act + 2 * hits + 10 * items      # adjacency, level checks, writes, items
     achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == expand_source_sha() else None
@@ -358,6 +359,7 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "gteps": e_act * ws * args.steps / t_dev / 1e9,
         "e_act_per_step": e_act,
+        "e_act_skipped_per_step": sum(s["e_act_skipped"] for s in stats),
         "batched_qps": batched,
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -157,6 +157,8 @@ typedef struct {
     int64_t work_items;     /* (frontier node, level) expansion items */
     int64_t frontier_nodes; /* sum over levels of |Q_l| (both runs) */
     int64_t kernels;        /* kernels the query launches when replayed from its CUDA graph */
+    int64_t e_act_skipped;  /* part of e_act_marginal whose expansion was skipped: the last
+                               marginal level, once its V_C nodes alone decide the outcome */
 } rpq_stats;
 
 /* Search one query (Sections 3-4): central run -> top-w CGs -> recovery of
@@ -307,22 +309,24 @@ int rpq_sync_device(rpq_kg *kg);
  *                         level's work (CSR entries) is at most
  *                         next_queue_mult x that limit (default 16)
  *   batch_slots           concurrent search slots of rpq_search_batch (8)
- *   flat_graph_max_depth  queries with max_depth up to this value replay a
- *                         flat CUDA graph, deeper ones a graph with a WHILE
- *                         node per run (12) */
+ *   flat_levels           Glevels per run replayed as plain CUDA-graph nodes;
+ *                         the rest run in a WHILE node that a run stopping
+ *                         earlier never enters (4; 0 = all levels in the
+ *                         loop, >= max_depth + 1 = no loop) */
 typedef struct {
     int32_t queue_div;
     int32_t next_queue_mult;
     int32_t batch_slots;
-    int32_t flat_graph_max_depth;
+    int32_t flat_levels;
 } rpq_tuning;
 
 int rpq_get_tuning(const rpq_kg *kg, rpq_tuning *out);
 /* Values < 1 are rejected (RPQ_EINVAL); captured CUDA graphs are rebuilt. */
 int rpq_set_tuning(rpq_kg *kg, const rpq_tuning *t);
 /* Autotuner: times the one-at-a-time search of the nq sample queries for each
- * queue_div in {8, 32, 128} x next_queue_mult in {4, 16, 64}, then
- * rpq_search_batch for batch_slots in {4, 8, 16}, keeps the fastest setting
+ * queue_div in {8, 32, 128} x next_queue_mult in {4, 16, 64}, then for
+ * flat_levels in {2, 3, 4, 6, 64}, then rpq_search_batch for batch_slots in
+ * {4, 8, 16}, keeps the fastest setting
  * (the median of `repeats` timed passes after one warm-up pass decides) and
  * returns it in *best (may be NULL).  Results are the same under every
  * setting. */

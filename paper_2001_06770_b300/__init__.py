@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
                 ("levels_central", ctypes.c_int32), ("levels_marginal", ctypes.c_int32),
                 ("n_cg", ctypes.c_int32), ("n_selected", ctypes.c_int32),
                 ("work_units", ctypes.c_int64), ("work_items", ctypes.c_int64), ("frontier_nodes", ctypes.c_int64),
-                ("kernels", ctypes.c_int64)]
+                ("kernels", ctypes.c_int64), ("e_act_skipped", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,7 +88,7 @@ class Completion(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("queue_div", ctypes.c_int32), ("next_queue_mult", ctypes.c_int32),
-                ("batch_slots", ctypes.c_int32), ("flat_graph_max_depth", ctypes.c_int32)]
+                ("batch_slots", ctypes.c_int32), ("flat_levels", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -33,16 +33,14 @@ int dev_err_to_status(uint32_t err) {
   return RPQ_EINTERNAL;
 }
 
-// Graph form of a query: a flat graph launches L+1 level pairs per run
-// (levels after the run stopped return at once); a loop graph runs the level
-// pair in a WHILE node as often as needed.  On B300 one WHILE iteration costs
-// more than two early-exit launches, so the flat form is used up to the
-// tuning's flat_graph_max_depth (default 12; RPQ_GRAPH_LOOP=1 / 0 forces
-// loops / flat graphs).
-static bool graph_loops(const rpq_kg* kg, int L) {
+// Levels per run launched as plain graph nodes before the WHILE node of a
+// query graph: the tuning's flat_levels, or RPQ_GRAPH_LOOP=1 (none: the loop
+// runs every level) / RPQ_GRAPH_LOOP=0 (all L+1: no loop).
+static int flat_levels(const rpq_kg* kg, int L) {
   static int v = -2;
   if (v == -2) { const char* e = getenv("RPQ_GRAPH_LOOP"); v = (e && *e) ? (*e == '0' ? 0 : 1) : -1; }
-  return v == -1 ? (L > kg->tune.flat_graph_max_depth) : (v == 1);
+  const int k = v == -1 ? kg->tune.flat_levels : (v == 1 ? 0 : L + 1);
+  return std::min(k, L + 1);
 }
 
 // Slot parameters that follow the tuning.  Graphs captured with other values
@@ -74,6 +72,22 @@ void destroy_slot(Slot* s) {
   delete s;
 }
 
+// The V_C check of the marginal run (k_target) and the skipped final
+// expansion it allows are on unless RPQ_NO_TARGET=1 (for comparisons).
+static bool use_target() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_NO_TARGET"); v = (e && *e == '1') ? 0 : 1; }
+  return v == 1;
+}
+
+// Smallest expansion (work units) worth the V_C check (RPQ_TARGET_MIN_WORK
+// overrides the default for comparisons).
+static uint32_t target_min_work() {
+  static long v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_TARGET_MIN_WORK"); v = (e && *e) ? std::max(0L, atol(e)) : (1L << 18); }
+  return uint32_t(v);
+}
+
 int create_slot(rpq_kg* kg, Slot** out) {
   Slot* s = new Slot();
   const size_t n = size_t(kg->dev.n);
@@ -97,9 +111,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.items, sizeof(Item) * d.cap);
   SA(d.imask, sizeof(uint16_t) * d.cap + 16);
   SA(d.cg, sizeof(uint32_t) * d.cap);
-  const size_t tk = n / 32 + 4096;
-  SA(d.topk[0], sizeof(uint32_t) * tk);
-  SA(d.topk[1], sizeof(uint32_t) * tk);
+  SA(d.topk, sizeof(uint32_t) * size_t(num_sms()) * 2 * kMaxK);   // k_topk runs 2 blocks per SM
   SA(d.rmask, sizeof(unsigned long long) * d.cap * kMaxCols);
   SA(d.vmask, sizeof(unsigned long long) * d.cap);
   SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
@@ -109,6 +121,8 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.fq[1], sizeof(uint32_t) * d.cap);
   SA(d.ulist, sizeof(uint32_t) * d.cap);
   SA(d.vcl, sizeof(uint32_t) * d.cap);
+  d.tgt_cap = d.cap;
+  SA(d.tgt, sizeof(uint32_t) * d.tgt_cap);
   SA(d.sticky, 16);
   SA(d.ctl, sizeof(Ctl));
   SA(d.q, sizeof(QueryDev));
@@ -133,6 +147,8 @@ int create_slot(rpq_kg* kg, Slot** out) {
   if (rc != RPQ_OK) { destroy_slot(s); return rc; }
   d.qlog = nullptr;
   d.qcap = 0;
+  d.target = use_target() ? 1u : 0u;
+  d.tgt_min_work = target_min_work();
   apply_tuning(kg, s);
   *out = s;
   return RPQ_OK;
@@ -203,62 +219,76 @@ int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty)
   return RPQ_OK;
 }
 
-// Graph of one query shape: captured segments as child graphs, and the level
-// loop of each run as a WHILE conditional node whose body (k_enqueue,
-// k_expand) repeats until k_expand ends it.
-static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, cudaGraphExec_t* out) {
+// Graph of one query shape.  The whole query is captured into one graph; the
+// level loop of each run is its first K levels as plain nodes (a level after
+// the run stopped costs an early-exit launch) followed, when K < L+1, by a
+// WHILE conditional node whose body (the level kernels) repeats until
+// k_expand clears the condition.  k_expand also clears it when the run stops
+// inside the first K levels, so a short run never enters the loop.  On B300 a
+// WHILE iteration costs more than the early-exit launches of a level, and
+// most runs stop within a few levels, hence a small plain prefix.
+static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, int L, int K, cudaGraphExec_t* out) {
   cudaGraph_t main = nullptr;
   RPQ_CUDA(cudaGraphCreate(&main, 0));
-  cudaGraphNode_t prev = nullptr;
+  cudaStream_t side = nullptr;
   int rc = RPQ_OK;
   auto fail = [&](const char* what, cudaError_t e) {
+    if (rc != RPQ_OK) return;
     cudaGetLastError();
     set_error(RPQ_ECUDA, "graph build (%s): %s", what, cudaGetErrorString(e));
     rc = RPQ_ECUDA;
   };
-  auto add_segment = [&](auto&& launch) {
+  bool capturing = false;
+  auto check = [&](const char* what, cudaError_t e) { if (e != cudaSuccess) fail(what, e); return e == cudaSuccess; };
+  auto add_run = [&](int run) {
     if (rc != RPQ_OK) return;
-    cudaGraph_t child = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { fail("begin capture", e); return; }
-    launch();
-    e = cudaStreamEndCapture(s->st, &child);
-    if (e != cudaSuccess) { if (child) cudaGraphDestroy(child); fail("end capture", e); return; }
-    cudaGraphNode_t node = nullptr;
-    e = cudaGraphAddChildGraphNode(&node, main, prev ? &prev : nullptr, prev ? 1 : 0, child);
-    cudaGraphDestroy(child);
-    if (e != cudaSuccess) { fail("child node", e); return; }
-    prev = node;
-  };
-  auto add_loop = [&](int run) {
-    if (rc != RPQ_OK) return;
+    if (K >= L + 1) {                                   // no loop: L+1 plain levels
+      for (int l = 0; l <= L; ++l) launch_level(kg->dev, s->d, run, s->st, nullptr, 0, false);
+      return;
+    }
     cudaGraphConditionalHandle h = 0;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) { fail("conditional handle", e); return; }
+    if (!check("conditional handle", cudaGraphConditionalHandleCreate(&h, main, 1, cudaGraphCondAssignDefault))) return;
+    for (int l = 0; l < K; ++l) launch_level(kg->dev, s->d, run, s->st, nullptr, h, true);
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if (!check("capture info", cudaStreamGetCaptureInfo(s->st, &status, nullptr, nullptr, &deps, nullptr, &ndeps))) return;
+    std::vector<cudaGraphNode_t> dv(deps, deps + ndeps);
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node = nullptr;
-    e = cudaGraphAddNode(&node, main, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, &cp);
-    if (e != cudaSuccess) { fail("conditional node", e); return; }
+    if (!check("conditional node", cudaGraphAddNode(&node, main, dv.empty() ? nullptr : dv.data(), nullptr,
+                                                    dv.size(), &cp))) return;
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(s->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) { fail("capture loop body", e); return; }
-    launch_level(kg->dev, s->d, run, s->st, nullptr, h, true);
+    if (!side && !check("side stream", cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking))) return;
+    if (!check("capture loop body", cudaStreamBeginCaptureToGraph(side, body, nullptr, nullptr, 0,
+                                                                  cudaStreamCaptureModeThreadLocal))) return;
+    launch_level(kg->dev, s->d, run, side, nullptr, h, true);
     cudaGraph_t got = nullptr;
-    e = cudaStreamEndCapture(s->st, &got);
-    if (e != cudaSuccess) { fail("end loop body", e); return; }
-    prev = node;
+    if (!check("end loop body", cudaStreamEndCapture(side, &got))) return;
+    check("loop dependency", cudaStreamUpdateCaptureDependencies(s->st, &node, nullptr, 1,
+                                                                  cudaStreamSetCaptureDependencies));
   };
-  add_segment([&] { launch_run_setup(kg->dev, s->d, 0, s->st, nullptr); });
-  add_loop(0);
-  add_segment([&] {
+  if (check("begin capture", cudaStreamBeginCaptureToGraph(s->st, main, nullptr, nullptr, 0,
+                                                            cudaStreamCaptureModeThreadLocal))) {
+    capturing = true;
+    launch_run_setup(kg->dev, s->d, 0, s->st, nullptr);
+    add_run(0);
     launch_select_recover(kg->dev, s->d, n_m, s->st, nullptr);
-    if (n_m > 0) launch_run_setup(kg->dev, s->d, 1, s->st, nullptr);
-  });
-  if (n_m > 0) add_loop(1);
-  add_segment([&] { launch_results(s->d, s->st, nullptr); });
+    if (n_m > 0) {
+      launch_run_setup(kg->dev, s->d, 1, s->st, nullptr);
+      add_run(1);
+    }
+    launch_results(s->d, s->st, nullptr);
+  }
+  if (capturing) {
+    cudaGraph_t got = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->st, &got);
+    if (e != cudaSuccess) fail("end capture", e);
+  }
+  if (side) cudaStreamDestroy(side);
   if (rc == RPQ_OK) {
     const cudaError_t e = cudaGraphInstantiate(out, main, 0);
     if (e != cudaSuccess) fail("instantiate", e);
@@ -275,17 +305,15 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
     return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof);
   }
   (void)n_c;
-  // a loop graph depends only on whether the query has marginal keywords; a
-  // flat graph also on L
-  const bool loops = !s->d.persistent && graph_loops(kg, L);
-  const uint64_t key = loops ? uint64_t(n_m > 0 ? 1 : 0) : ((uint64_t(L) << 8) | uint64_t(n_m > 0 ? 3 : 2));
+  const int K = s->d.persistent ? L + 1 : flat_levels(kg, L);
+  const uint64_t key = (uint64_t(L) << 16) | (uint64_t(K) << 8) | uint64_t(n_m > 0 ? 1 : 0);
   auto it = s->graphs.find(key);
   if (it == s->graphs.end()) {
     cudaGraphExec_t exec = nullptr;
-    if (loops) {
-      const int rc = build_query_graph(kg, s, n_m, &exec);
+    if (!s->d.persistent) {
+      const int rc = build_query_graph(kg, s, n_m, L, K, &exec);
       if (rc != RPQ_OK) return rc;
-    } else {
+    } else {                                            // one persistent kernel per run
       cudaGraph_t graph = nullptr;
       RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
       const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr);
@@ -333,6 +361,7 @@ void fill_stats(const Ctl& c, rpq_stats* st) {
   st->work_units = int64_t(c.units);
   st->work_items = int64_t(c.items);
   st->frontier_nodes = int64_t(c.frontier);
+  st->e_act_skipped = int64_t(c.e_act_skip);
 }
 
 // Wait for the slot's query and copy its results out.
@@ -350,7 +379,7 @@ int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats
   if (stats) {
     const int runs = 1 + (s->pending_nm > 0 && c.levels[1] >= 0 ? 1 : 0);
     stats->kernels = kernels_fixed_per_query(s->pending_nm) +
-                     (s->d.persistent ? runs : 2 * int64_t(c.iters[0] + c.iters[1]));
+                     (s->d.persistent ? runs : 2 * int64_t(c.iters[0]) + 3 * int64_t(c.iters[1]));
   }
   return RPQ_OK;
 }
@@ -542,6 +571,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   DevSlot d = s->d;
   d.qlog = d_qlog;
   d.qcap = uint32_t(qcap);
+  d.target = 0;            // every level expanded in full: the frontiers are part of the trace
   std::vector<uint8_t> H(size_t(s->d.hp) * kMaxCols), vis(((n + 3) / 4) * 4);
   std::vector<uint32_t> qlog;
   Ctl c{};
@@ -657,7 +687,7 @@ int rpq_get_tuning(const rpq_kg* kg, rpq_tuning* out) {
 
 int rpq_set_tuning(rpq_kg* kg, const rpq_tuning* t) {
   if (!kg || !t) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
-  if (t->queue_div < 1 || t->next_queue_mult < 1 || t->batch_slots < 1 || t->flat_graph_max_depth < 0) {
+  if (t->queue_div < 1 || t->next_queue_mult < 1 || t->batch_slots < 1 || t->flat_levels < 0) {
     set_error(RPQ_EINVAL, "tuning values must be positive");
     return RPQ_EINVAL;
   }
@@ -713,6 +743,14 @@ int rpq_autotune(rpq_kg* kg, const rpq_query* qs, int32_t nq, int32_t repeats, r
       if ((rc = time_single(&sec)) != RPQ_OK) return rc;
       if (sec < best_s) { best_s = sec; bestt = cur; }
     }
+  }
+  cur = bestt;
+  for (int fl : {2, 3, 4, 6, 64}) {
+    cur.flat_levels = fl;
+    if ((rc = rpq_set_tuning(kg, &cur)) != RPQ_OK) return rc;
+    double sec = 0;
+    if ((rc = time_single(&sec)) != RPQ_OK) return rc;
+    if (sec < best_s) { best_s = sec; bestt.flat_levels = fl; }
   }
   cur = bestt;
   best_s = 1e30;

@@ -86,7 +86,7 @@ struct rpq_kg {
   std::vector<int64_t> kw_ptr;   // host copy of the postings offsets
   std::vector<rpq::Slot*> slots; // search slots, created on first use
   rpq::Prof* prof = nullptr;      // profiling mode when non-NULL
-  rpq_tuning tune{32, 16, 8, 12}; // work-split parameters (rpq_set_tuning / rpq_autotune)
+  rpq_tuning tune{32, 16, 8, 4};  // work-split parameters (rpq_set_tuning / rpq_autotune)
   rpq::SgScratch* sg = nullptr;   // result-subgraph lists (rpq_search_subgraphs), grown on demand
 };
 

@@ -89,6 +89,10 @@ struct Ctl {
   uint32_t nq[2];              // |Q_l| per level parity
   uint32_t n_matched;          // selected CGs matched so far (marginal run)
   uint32_t rpg_stop;           // Theorem 4 ended the marginal run (w > k)
+  uint32_t skip_lvl;           // l + 1: the expansion of Glevel l cannot change the outcome (k_target)
+  uint32_t tgt_n, tgt_done;    // k_target: (column, node) hits found, blocks finished
+  unsigned long long eact_lvl[2];  // E_act of the level being enqueued, per level parity
+  unsigned long long e_act_skip;   // E_act of skipped expansions
   uint32_t qlog_n;             // entries of the frontier log (trace mode)
   uint32_t ncg;                // CGs identified (central run)
   uint32_t err;                // DevErr bits
@@ -102,7 +106,7 @@ struct Ctl {
   uint32_t iters[2];           // level kernel pairs executed per run
   uint32_t fq_use[2];          // the queue of this parity is being filled
   uint32_t n_res;
-  uint32_t topk_n[2];          // element counts of the top-k pass buffers
+  uint32_t topk_done;          // k_topk: blocks finished
   unsigned long long e_act[2];  // per run
   unsigned long long hits[2];
   unsigned long long units, items, frontier;  // work totals of both runs
@@ -122,7 +126,7 @@ struct DevSlot {
   Item* items;
   uint16_t* imask;            // column masks of the items
   uint32_t* cg;
-  uint32_t* topk[2];
+  uint32_t* topk;             // k_topk: survivors of each block (w per block)
   unsigned long long* rmask;  // recovery: per-column CG mask per node (kMaxCols * cap)
   unsigned long long* vmask;  // recovery: union over columns
   uint32_t* rlist;            // recovery: per-column node lists (kMaxCols * cap)
@@ -137,6 +141,10 @@ struct DevSlot {
   uint32_t cap;               // capacity (elements) of items/cg/lists
   uint32_t* qlog;             // trace mode: (level << 26 | node) of every Q_l entry
   uint32_t qcap;
+  uint32_t* tgt;              // k_target: (column << 26 | node) hits of V_C nodes
+  uint32_t tgt_cap;
+  uint32_t target;            // marginal run: check V_C first and skip a final expansion
+  uint32_t tgt_min_work;      // ... on levels with at least this many work units
   uint32_t* sticky;           // device error bits kept across queries
   unsigned* bar;              // grid barrier of the persistent run kernel: count, generation
   uint32_t persistent;        // run each level loop as one cooperative k_run launch

@@ -6,17 +6,21 @@
 //     k_run_start, memsets of vis / F / cf, k_seed (Section 4.2.1)
 //     per Glevel l:  k_enqueue        frontier enqueue + reset (4.2.2) and
 //                                     result identification (4.2.3,
-//                                     Theorem 3; PTC stop; RPG match)
+//                                     Theorem 3; PTC stop; RPG match;
+//                                     Theorem 4); E_act of the level
+//                    k_target         marginal run only: hits of level l+1
+//                                     on V_C, and whether they decide the run
 //                    k_expand         termination decision + expansion
 //                                     (Algorithm 1) of the newly active edges
-//   after the central run: k_topk_pass x4, k_select (top-w CGs),
+//   after the central run: k_topk (top-w CGs),
 //                          k_recover_cols, k_recover_vc (Algorithm 2 -> V_C)
 //   at the end:            k_results (Eq. 6, top-k by (S^r, id))
-// The Glevel is kept in the control block, so the two level kernels form the
-// body of a CUDA-graph WHILE node that k_expand ends when the run stops; the
-// graph of each query shape (|C|, |M|, L) is built once and replayed.  Without
-// a graph (profiling, tracing) the host launches L+1 level pairs and the
-// kernels of finished runs return at once.
+// The Glevel is kept in the control block, so the level kernels form the body
+// of a CUDA-graph WHILE node that k_expand ends when the run stops, or the
+// L+1 early-exit repetitions of a flat graph; the graph of each query shape
+// (|C|, |M|, L) is built once and replayed.  Without a graph (profiling,
+// tracing) the host launches the same sequence and the kernels of finished
+// runs return at once.
 //
 // Exactness: the expansion at level l touches, for frontier node v and
 // column j, only the edges with max(h[v][j], a) == l (the rows are sorted by
@@ -39,10 +43,11 @@ constexpr int kEnqThreads = 256;
 constexpr int kEnqRounds = 4;
 constexpr int kExpThreads = 256;
 constexpr int kExpRounds = 4;                      // 32-unit rounds per warp tile
+constexpr int kTgtThreads = 256;
 constexpr int kWarpTile = 32 * kExpRounds;         // 128 work units per warp tile
 constexpr int kRecThreads = 1024;
 constexpr int kTopkThreads = 1024;
-constexpr int kTopkChunk = 4096;
+constexpr int kTopkChunk = 4096;                   // keys per block and round of the top-w selection
 constexpr unsigned long long kWorkBits = 38;
 constexpr unsigned long long kWorkMask = (1ull << kWorkBits) - 1ull;
 
@@ -96,6 +101,9 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->fq_use[1] = 0;
   c->lvl_enq = c->lvl_exp = 0;
   c->level = 0;
+  c->eact_lvl[0] = c->eact_lvl[1] = 0;
+  c->skip_lvl = 0;
+  c->tgt_n = c->tgt_done = 0;
   s.bar[0] = 0;                      // barrier arrivals of the persistent kernel
   c->last_expanded = -1;
 }
@@ -178,7 +186,9 @@ __device__ __forceinline__ double rpg_score(const QueryDev& q, uint32_t sc, uint
 // a CG still unmatched matches at level l+1 or later, so its RPG scores at
 // least rpg_score(S^c, l+1); the run may stop when every such bound ranks
 // after the k-th matched RPG on (score, node id), the ranking order.
-__device__ bool theorem4_stop(const Ctl* c, const QueryDev& q, uint32_t nsel, uint32_t l) {
+// `matched` and `sm` may be the control block's or a prospective copy.
+__device__ bool theorem4_stop(const Ctl* c, const uint8_t* matched, const uint8_t* sm, const QueryDev& q,
+                              uint32_t nsel, uint32_t l) {
   unsigned long long used = 0;
   double srk = 0.0;
   int32_t idk = -1;
@@ -186,8 +196,8 @@ __device__ bool theorem4_stop(const Ctl* c, const QueryDev& q, uint32_t nsel, ui
     int best = -1;
     double bs = 0.0;
     for (uint32_t gi = 0; gi < nsel; ++gi) {
-      if (!c->matched[gi] || ((used >> gi) & 1ull)) continue;
-      const double v = rpg_score(q, c->sel_sc[gi], c->sm[gi]);
+      if (!matched[gi] || ((used >> gi) & 1ull)) continue;
+      const double v = rpg_score(q, c->sel_sc[gi], sm[gi]);
       if (best < 0 || v < bs || (v == bs && c->sel[gi] < c->sel[best])) { best = int(gi); bs = v; }
     }
     if (best < 0) return false;
@@ -196,7 +206,7 @@ __device__ bool theorem4_stop(const Ctl* c, const QueryDev& q, uint32_t nsel, ui
     idk = c->sel[best];
   }
   for (uint32_t gi = 0; gi < nsel; ++gi) {
-    if (c->matched[gi]) continue;
+    if (matched[gi]) continue;
     const double b = rpg_score(q, c->sel_sc[gi], l + 1);
     if (!(b > srk || (b == srk && c->sel[gi] > idk))) return false;
   }
@@ -250,7 +260,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         nm += c->matched[gi];
       }
       c->n_matched = nm;
-      if (nm < nsel && nm >= uint32_t(q.k)) c->rpg_stop = theorem4_stop(c, q, nsel, l) ? 1u : 0u;
+      if (nm < nsel && nm >= uint32_t(q.k)) c->rpg_stop = theorem4_stop(c, c->matched, c->sm, q, nsel, l) ? 1u : 0u;
     }
   }
 
@@ -267,6 +277,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   // spread over many blocks), kEnqRounds words per warp for the bitmap
   const uint32_t kTile = sparse ? uint32_t(kEnqThreads) : uint32_t(kEnqThreads * kEnqRounds);
   uint32_t qcount = 0;
+  uint64_t eact = 0;                                   // E_act of this level (Algorithm 1's activations)
   for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
     uint32_t it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
     // candidate node of each round: bitmap mode, word tile/32 + r*nwarp + warp
@@ -357,6 +368,10 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
           it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
           ++my_items;
           my_work += hi - lo;
+          // every eq column activates the prefix a <= l, every lt column the segment a == l
+          uint32_t seg_l = lo;
+          if (eq && lt) seg_l = (indexed && l <= kLvxLevels) ? rb + o_lo : seg_lower(g.adj, rb, hi, l);
+          eact += uint64_t(__popc(eq)) * (hi - rb) + uint64_t(__popc(lt)) * (hi - seg_l);
         }
       }
       if (sparse) {                                     // nodes of a warp lie in different words
@@ -398,7 +413,9 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
     __syncthreads();
   }
   const uint64_t qt = block_sum(qcount, s_warp);
+  const uint64_t et = block_sum(eact, s_warp);
   if (threadIdx.x == 0 && qt) atomicAdd(&c->nq[p], uint32_t(qt));
+  if (threadIdx.x == 0 && et) atomicAdd(&c->eact_lvl[p], (unsigned long long)et);
 }
 
 __global__ void __launch_bounds__(kEnqThreads)
@@ -408,6 +425,123 @@ k_enqueue(DevKG g, DevSlot s, int run) {
   const uint32_t l = c->lvl_enq;
   if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
   enqueue_level<false>(g, s, run, l);
+}
+
+// ------------------------------------------- level: V_C check (marginal run)
+// Between the enqueue and the expansion of marginal Glevel l.  The first hits
+// of level l+1 on the V_C nodes of still unmatched CGs are found from the
+// receiving side: node v is first hit in column j at l+1 exactly when some
+// neighbour u expands to it at level l, i.e. u was reached with
+// max(h_uj, a_uv) = l and u had not stopped by then (Algorithm 1,
+// Definition 8; the levels are symmetric).  One warp per (V_C node, column)
+// scans v's entries with a <= l and stops at the first such u; the scan
+// writes nothing.  The last block to finish applies the hits (h = l+1,
+// visited bit, F_{l+1}, the frontier queue of l+1 when it is in use: the
+// same writes the expansion would make) and runs the identification of
+// level l+1 on V_C alone.  When that shows the run stops at l+1 (every
+// selected CG matched, Theorem 4, or l+1 = L) and some hit was applied (so
+// Q_{l+1} is not empty), nothing else the expansion of level l would compute
+// can reach the results, and k_expand skips it.  Levels with fewer than
+// tgt_min_work work units are left alone (the check would cost more than the
+// expansion).  Off in trace mode, where every frontier is compared.
+__global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
+  Ctl* c = s.ctl;
+  if (c->done || !s.target) return;
+  const QueryDev& q = *s.q;
+  const uint32_t l = c->lvl_exp;
+  const int p = int(l & 1u);
+  const uint32_t nsel = c->nsel;
+  const int nm = q.n_m;
+  // the run ends at level l anyway (the stop test of k_expand), or the level
+  // is too small for a skip to pay for the check
+  if (nm == 0 || c->nq[p] == 0 || c->n_matched >= nsel || c->rpg_stop || l >= uint32_t(q.L)) return;
+  if ((c->work[p] & kWorkMask) < s.tgt_min_work) return;
+  const uint32_t nvc = min(c->nvc, s.cap);
+  const uint32_t ntask = nvc * uint32_t(nm);
+  const uint32_t lane = lane_id();
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = gw; t < ntask; t += nwarps) {
+    const uint32_t pr = s.vcl[t / uint32_t(nm)];
+    const uint32_t j = t % uint32_t(nm);
+    const uint32_t gi = pr >> kNodeBits, v = pr & kNodeMask;
+    if (c->matched[gi] || ((vis_byte(s.vis, v) >> j) & 1u)) continue;   // same in every lane
+    const uint32_t rb = g.row_ptr[v];
+    const uint32_t hi = seg_at(g, v, rb, g.row_ptr[v + 1], l + 1);      // entries with a <= l
+    bool found = false;
+    for (uint32_t e0 = rb; e0 < hi && !found; e0 += 32u) {
+      const uint32_t e = e0 + lane;
+      bool par = false;
+      if (e < hi) {
+        const uint32_t x = __ldg(g.adj + e);
+        const uint32_t a = x >> kNodeBits, u = x & kNodeMask;
+        if ((vis_byte(s.vis, u) >> j) & 1u) {
+          const uint32_t hu = s.H[size_t(j) * s.hp + u];
+          const uint32_t lam = a > hu ? a : hu;
+          par = lam == l && !(((s.cf[u >> 5] >> (u & 31u)) & 1u) && s.stopl[u] <= l);
+        }
+      }
+      found = __any_sync(0xffffffffu, par);
+    }
+    if (found && lane == 0) {
+      const uint32_t i = atomicAdd(&c->tgt_n, 1u);
+      if (i < s.tgt_cap) s.tgt[i] = (j << kNodeBits) | v;
+    }
+  }
+  __shared__ uint32_t s_last, s_hits;
+  __shared__ uint32_t s_acc[kMaxK];
+  __shared__ uint8_t s_matched[kMaxK], s_sm[kMaxK];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->tgt_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    s_hits = 0;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t nf = __ldcg(&c->tgt_n);
+  const bool over = nf > s.tgt_cap;                     // too many to list: expand in full
+  uint32_t* Fn = s.F[p ^ 1];
+  const bool push = __ldcg(&c->fq_use[p ^ 1]) != 0;
+  uint32_t hits = 0;
+  for (uint32_t i = threadIdx.x; !over && i < nf; i += blockDim.x) {
+    const uint32_t x = __ldcg(s.tgt + i), j = x >> kNodeBits, v = x & kNodeMask;
+    s.H[size_t(j) * s.hp + v] = uint8_t(l + 1);         // a repeated (node, column) writes the same value
+    const uint32_t old = atomicOr(s.vis + (v >> 2), (1u << j) << ((v & 3u) * 8u));
+    if ((old >> ((v & 3u) * 8u + j)) & 1u) continue;
+    ++hits;
+    const uint32_t of = atomicOr(Fn + (v >> 5), 1u << (v & 31u));
+    if (push && !((of >> (v & 31u)) & 1u) && !__ldcg(&c->fq_over[p ^ 1])) {
+      const uint32_t b = atomicAdd(&c->fq_n[p ^ 1], 1u);
+      if (b + 1u > s.fq_limit) atomicExch(&c->fq_over[p ^ 1], 1u); else s.fq[p ^ 1][b] = v;
+    }
+  }
+  if (hits) atomicAdd(&s_hits, hits);
+  for (uint32_t i = threadIdx.x; i < uint32_t(kMaxK); i += blockDim.x) s_acc[i] = 0;
+  __syncthreads();
+  // identification of level l+1 restricted to V_C (the RPG match of k_enqueue)
+  for (uint32_t i = threadIdx.x; i < nvc; i += blockDim.x) {
+    const uint32_t pr = s.vcl[i];
+    atomicOr(&s_acc[pr >> kNodeBits], uint32_t(__ldcg(reinterpret_cast<const uint8_t*>(s.vis) + (pr & kNodeMask))));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t full = (1u << nm) - 1u;
+    uint32_t cnt = 0;
+    for (uint32_t gi = 0; gi < nsel; ++gi) {
+      const bool was = c->matched[gi] != 0;
+      s_matched[gi] = (was || (s_acc[gi] & full) == full) ? 1 : 0;
+      s_sm[gi] = was ? c->sm[gi] : uint8_t(l + 1);
+      cnt += s_matched[gi];
+    }
+    const bool stop_next = l + 1 >= uint32_t(q.L) || cnt >= nsel ||
+                           (cnt >= uint32_t(q.k) && theorem4_stop(c, s_matched, s_sm, q, nsel, l + 1));
+    if (!over && s_hits && stop_next) c->skip_lvl = l + 1;
+    if (s_hits) atomicAdd(&c->hits[1], (unsigned long long)s_hits);
+    c->tgt_n = 0;
+    c->tgt_done = 0;
+  }
 }
 
 // ----------------------------------------------------------- level: expand
@@ -449,16 +583,25 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.w))
                              : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel) || ldx<P>(&c->rpg_stop));
   const bool stop = (nq == 0) || term || (l >= uint32_t(q.L));
+  // k_target found that the V_C nodes alone decide the outcome at level l+1
+  const bool skip = !stop && ldx<P>(&c->skip_lvl) == l + 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->level = l;
     c->frontier += nq;
+    const unsigned long long ea = ldx<P>(&c->eact_lvl[p]);   // enqueued activations of this level
+    c->eact_lvl[p] = 0;
     if (stop) {
       c->done = 1;
       c->levels[run] = (nq == 0 && l > 0) ? int32_t(l) - 1 : int32_t(l);
       if (in_graph) cudaGraphSetConditional(loop, 0);
     } else {
-      c->units += n_work;
-      c->items += n_items;
+      c->e_act[run] += ea;
+      if (skip) {
+        c->e_act_skip += ea;
+      } else {
+        c->units += n_work;
+        c->items += n_items;
+      }
       c->last_expanded = int32_t(l);
       c->levels[run] = int32_t(l);   // provisional; final when the run stops
       c->lvl_enq = l + 1;
@@ -468,7 +611,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       c->fq_over[p] = 0;
     }
   }
-  if (stop || n_work == 0) return stop;
+  if (stop || skip || n_work == 0) return stop;
 
   __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[p ^ 1];
@@ -482,7 +625,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t ntiles = (n_work + kWarpTile - 1) / kWarpTile;
-  uint64_t eact = 0, hits = 0;
+  uint64_t hits = 0;
   for (uint32_t t = gw; t < ntiles; t += nwarps) {
     const uint32_t t0 = t * kWarpTile;
     const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
@@ -527,7 +670,6 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       const uint32_t a = x_r[r] >> kNodeBits;
       const uint32_t eq = m_r[r] & 0xffu, lt = m_r[r] >> 8;
       const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
-      eact += __popc(act);
       nw_r[r] = act & ~vb_r[r];
     }
 #pragma unroll
@@ -553,12 +695,8 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       queue_push(s, c, p ^ 1, use_next, fresh, nb);
     }
   }
-  const uint64_t te = block_sum(eact, s_warp);
   const uint64_t th = block_sum(hits, s_warp);
-  if (threadIdx.x == 0) {
-    if (te) atomicAdd(&c->e_act[run], (unsigned long long)te);
-    if (th) atomicAdd(&c->hits[run], (unsigned long long)th);
-  }
+  if (threadIdx.x == 0 && th) atomicAdd(&c->hits[run], (unsigned long long)th);
   return false;
 }
 
@@ -621,68 +759,137 @@ k_run(DevKG g, DevSlot s, int run) {
 }
 
 // ------------------------------------------------------ top-w CG selection
-// Block-local top-K merge: each block sorts a chunk of up to kTopkChunk keys
-// in shared memory (bitonic) and keeps its K smallest; passes repeat on the
-// survivors.  Keys are (level << 26) | node, so ascending order is the
-// (S^c, node id) order of the selection; 0xffffffff pads short chunks.
-__global__ void __launch_bounds__(kTopkThreads)
-k_topk_pass(DevSlot s, int pass) {
+// One launch.  Keys are (S^c << 26) | node, so ascending order is the
+// (S^c, node id) order of the selection.  Each block takes chunks of up to
+// kTopkChunk CG keys and keeps the w smallest it has seen (the w-th smallest
+// of a chunk is found by a three-round radix select over 12/10/10-bit digits
+// with shared-memory histograms; only keys up to it are kept); the last block
+// to finish selects the w smallest of all blocks' survivors the same way,
+// orders them by rank and writes the selected CGs.
+
+// The K-th smallest (1-based, K <= number of valid keys) of keys[0..len);
+// 0xffffffff marks an empty entry.  All threads of the block call it.
+__device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
+                                  uint64_t* s_warp, uint32_t* s_bin) {
+  uint32_t prefix = 0, pmask = 0, need = K;
+  const uint32_t nt = blockDim.x;
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    const uint32_t bits = r == 0 ? 12u : 10u, sh = r == 0 ? 20u : (r == 1 ? 10u : 0u);
+    const uint32_t B = 1u << bits, per = (B + nt - 1) / nt;
+    for (uint32_t i = threadIdx.x; i < B; i += nt) hist[i] = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < len; i += nt) {
+      const uint32_t k = keys[i];
+      if (k != 0xffffffffu && (k & pmask) == prefix) atomicAdd(&hist[(k >> sh) & (B - 1u)], 1u);
+    }
+    __syncthreads();
+    uint32_t local = 0;
+    for (uint32_t b = threadIdx.x * per; b < min(B, (threadIdx.x + 1) * per); ++b) local += hist[b];
+    uint64_t tot = 0;
+    uint32_t run = uint32_t(block_excl_scan(local, s_warp, &tot));
+    for (uint32_t b = threadIdx.x * per; b < min(B, (threadIdx.x + 1) * per); ++b) {
+      if (run < need && need <= run + hist[b]) { s_bin[0] = b; s_bin[1] = run; }
+      run += hist[b];
+    }
+    __syncthreads();
+    need -= s_bin[1];
+    prefix |= s_bin[0] << sh;
+    pmask |= (B - 1u) << sh;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+// Keep the (at most) K smallest valid keys of keys[0..len) in place; returns their count.
+__device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
+                                        uint64_t* s_warp, uint32_t* s_bin) {
+  for (uint32_t i = threadIdx.x; i < 2; i += blockDim.x) s_bin[2 + i] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+    if (keys[i] != 0xffffffffu) atomicAdd(&s_bin[2], 1u);
+  __syncthreads();
+  const uint32_t valid = s_bin[2];
+  const uint32_t t = valid > K ? block_kth_key(keys, len, K, hist, s_warp, s_bin) : 0xfffffffeu;
+  // compact keys <= t to the front (order is restored by the final ranking)
+  uint32_t mine[kTopkChunk / kTopkThreads];
+  uint32_t nm = 0;
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
+    if (keys[i] <= t) mine[nm++] = keys[i];
+  __syncthreads();
+  for (uint32_t r = 0; r < nm; ++r) keys[atomicAdd(&s_bin[3], 1u)] = mine[r];
+  __syncthreads();
+  return min(valid, K);
+}
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
   Ctl* c = s.ctl;
   const uint32_t K = uint32_t(s.q->w);                   // beam width w
-  const uint32_t* src = pass == 0 ? s.cg : s.topk[(pass - 1) & 1];
-  const uint32_t n_in = pass == 0 ? c->ncg : c->topk_n[(pass - 1) & 1];
-  uint32_t* dst = s.topk[pass & 1];
-  const bool sorted_in = pass > 0 && n_in <= K;
-  const uint32_t nchunks = sorted_in ? 1 : (n_in + kTopkChunk - 1) / kTopkChunk;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->topk_n[pass & 1] = sorted_in ? n_in : min(n_in, nchunks * K);
-  if (sorted_in) {                     // already reduced: copy through
-    if (blockIdx.x == 0) for (uint32_t i = threadIdx.x; i < n_in; i += blockDim.x) dst[i] = src[i];
-    return;
-  }
-  __shared__ uint32_t key[kTopkChunk];
+  const uint32_t n_in = min(c->ncg, s.cap);
+  const uint32_t nchunks = (n_in + kTopkChunk - 1) / kTopkChunk;
+  __shared__ uint32_t key[kTopkChunk + 2 * kMaxK];
+  __shared__ uint32_t hist[4096];
+  __shared__ uint64_t s_warp[33];
+  __shared__ uint32_t s_bin[4];
+  __shared__ uint32_t s_keep, s_last;
+  uint32_t* keep = key + kTopkChunk;                     // survivors of this block (<= 2K while merging)
+  if (threadIdx.x == 0) s_keep = 0;
+  __syncthreads();
   for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const uint32_t b = ch * kTopkChunk;
     const uint32_t len = min(uint32_t(kTopkChunk), n_in - b);
-    uint32_t sz = 32;                               // sort only a power of two >= len
-    while (sz < len) sz <<= 1;
-    for (uint32_t i = threadIdx.x; i < sz; i += blockDim.x) key[i] = i < len ? src[b + i] : 0xffffffffu;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) key[i] = s.cg[b + i];
     __syncthreads();
-    for (uint32_t k = 2; k <= sz; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        for (uint32_t i = threadIdx.x; i < sz; i += blockDim.x) {
-          const uint32_t p = i ^ j;
-          if (p > i) {
-            const uint32_t a = key[i], bb = key[p];
-            const bool up = (i & k) == 0;
-            if ((a > bb) == up) { key[i] = bb; key[p] = a; }
-          }
-        }
-        __syncthreads();
-      }
+    const uint32_t m = block_keep_smallest(key, len, K, hist, s_warp, s_bin);
+    // merge with the survivors of earlier chunks
+    const uint32_t k0 = s_keep;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) keep[k0 + i] = key[i];
+    __syncthreads();
+    const uint32_t mm = block_keep_smallest(keep, k0 + m, K, hist, s_warp, s_bin);
+    if (threadIdx.x == 0) s_keep = mm;
+    __syncthreads();
+  }
+  uint32_t* out = s.topk + size_t(blockIdx.x) * K;
+  for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) out[i] = i < s_keep ? keep[i] : 0xffffffffu;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->topk_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last block: the K smallest of all survivors (blocks that had a chunk)
+  const uint32_t nb = min(nchunks, gridDim.x);
+  uint32_t total = 0;
+  for (uint32_t blk = 0; blk < nb; ++blk) {            // gather, reducing whenever the buffer fills
+    for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) key[total + i] = __ldcg(s.topk + size_t(blk) * K + i);
+    total += K;
+    if (total + K > uint32_t(kTopkChunk) || blk + 1 == nb) {
+      __syncthreads();
+      total = block_keep_smallest(key, total, K, hist, s_warp, s_bin);
+      __syncthreads();
     }
-    const uint32_t keep = min(K, len);
-    for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) dst[ch * K + i] = i < keep ? key[i] : 0xffffffffu;
-    __syncthreads();
   }
-}
-
-__global__ void k_select(DevSlot s, int last_pass) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Ctl* c = s.ctl;
-  const uint32_t K = uint32_t(s.q->w);
-  const uint32_t* src = s.topk[last_pass & 1];
-  const uint32_t n = min(c->topk_n[last_pass & 1], K);
-  uint32_t ns = 0;
-  for (uint32_t i = 0; i < n; ++i) {
-    const uint32_t key = src[i];
-    if (key == 0xffffffffu) break;
-    c->sel[ns] = int32_t(key & kNodeMask);
-    c->sel_sc[ns] = uint8_t(key >> kNodeBits);
-    ++ns;
+  // rank the (at most K) selected keys: ascending (S^c, node id)
+  __shared__ uint32_t s_sel[kMaxK];
+  for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const uint32_t v = key[i];
+    uint32_t rank = 0;
+    for (uint32_t o = 0; o < total; ++o) rank += key[o] < v;
+    s_sel[rank] = v;
   }
-  c->nsel = ns;
-  c->ulist_n = 0;
-  c->nvc = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (uint32_t i = 0; i < total; ++i) {
+      c->sel[i] = int32_t(s_sel[i] & kNodeMask);
+      c->sel_sc[i] = uint8_t(s_sel[i] >> kNodeBits);
+    }
+    c->nsel = total;
+    c->ulist_n = 0;
+    c->nvc = 0;
+    c->topk_done = 0;
+  }
 }
 
 // ---------------------------------------------------------------- recovery
@@ -853,7 +1060,6 @@ __global__ void k_results(DevSlot s) {
 }  // namespace
 
 // ------------------------------------------------------------ launchers
-constexpr int kTopkPasses = 4;
 
 // Launch wrapper: brackets the launch with CUDA events in profiling mode.
 template <typename F>
@@ -912,12 +1118,15 @@ void launch_run_persistent(const DevKG& g, const DevSlot& s, int run, cudaStream
   });
 }
 
-// One Glevel: enqueue + identification, then termination + expansion.
+// One Glevel: enqueue + identification, (marginal run) the V_C check, then
+// termination + expansion.
 void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
                   cudaGraphConditionalHandle loop, bool in_graph) {
   static const int enq_grid = one_wave_grid(k_enqueue, kEnqThreads);
   static const int exp_grid = one_wave_grid(k_expand, kExpThreads);
+  static const int tgt_grid = num_sms() * 2;
   timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_grid, kEnqThreads, 0, st>>>(g, s, run); });
+  if (run == 1) timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_target<<<tgt_grid, kTgtThreads, 0, st>>>(g, s); });
   timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<exp_grid, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
 }
 
@@ -925,8 +1134,7 @@ void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Pr
 void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof) {
   const int sms = num_sms();
   timed(prof, RPQ_PROF_TOPK, st, [&] {
-    for (int pass = 0; pass < kTopkPasses; ++pass) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, pass);
-    k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(s);
   });
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
@@ -960,8 +1168,7 @@ int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st
   for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
   const int sms = num_sms();
   timed(prof, RPQ_PROF_TOPK, st, [&] {
-    for (int pass = 0; pass < kTopkPasses; ++pass) k_topk_pass<<<sms * 2, kTopkThreads, 0, st>>>(s, pass);
-    k_select<<<1, 32, 0, st>>>(s, kTopkPasses - 1);
+    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(s);
   });
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
@@ -983,7 +1190,7 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
 // kernels plus, per run, two per executed Glevel or one persistent launch.
 int kernels_fixed_per_query(int n_m) {
   const int run = 2;                                // k_run_start, k_seed
-  return 1 + run + kTopkPasses + 1 + (n_m > 0 ? 2 + run : 0) + 1;
+  return 1 + run + 1 + (n_m > 0 ? 2 + run : 0) + 1;
 }
 
 }  // namespace rpq

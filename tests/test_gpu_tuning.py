@@ -23,7 +23,7 @@ def small():
 
 
 @pytest.mark.parametrize("tune", [dict(queue_div=1, next_queue_mult=1000), dict(queue_div=1 << 30, next_queue_mult=1),
-                                  dict(queue_div=4, next_queue_mult=1), dict(flat_graph_max_depth=0),
+                                  dict(queue_div=4, next_queue_mult=1), dict(flat_levels=0), dict(flat_levels=2), dict(flat_levels=64),
                                   dict(batch_slots=1), dict(batch_slots=16)])
 def test_results_do_not_depend_on_tuning(small, tune):
     ds, kg, qs, orc = small
