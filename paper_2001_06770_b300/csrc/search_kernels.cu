@@ -33,9 +33,13 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "rpq_host.h"
 
 namespace rpq {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -46,6 +50,7 @@ constexpr int kExpRounds = 4;                      // 32-unit rounds per warp ti
 constexpr int kTgtThreads = 256;
 constexpr int kWarpTile = 32 * kExpRounds;         // 128 work units per warp tile
 constexpr int kRecThreads = 1024;
+constexpr int kRecCluster = 8;                     // CTAs sweeping one keyword column
 constexpr int kTopkThreads = 1024;
 constexpr int kTopkChunk = 4096;                   // keys per block and round of the top-w selection
 constexpr unsigned long long kWorkBits = 38;
@@ -391,23 +396,40 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
     const uint64_t pre = block_excl_scan(packed, s_warp, &tot);
     if (threadIdx.x == 0) s_base = atomicAdd(&c->work[p], (unsigned long long)tot);
     __syncthreads();
-    if (my_items) {
+    {
       uint32_t idx = uint32_t((s_base >> kWorkBits) + (pre >> kWorkBits));
       uint32_t off = uint32_t((s_base & kWorkMask) + (pre & kWorkMask));
 #pragma unroll
-      for (int r = 0; r < kEnqRounds; ++r) {
-        if (!it_len[r]) continue;
-        Item it;
-        it.seg_begin = it_seg[r];
-        it.off = off;
-        s.items[idx] = it;
-        s.imask[idx] = uint16_t(it_msk[r]);
-        const uint32_t last = off + it_len[r] - 1;     // warp tiles starting inside the item
-        for (uint32_t t = (off + kWarpTile - 1) / kWarpTile; t <= last / kWarpTile; ++t) {
-          if (t < s.tile_cap) s.tile_first[t] = idx; else atomicOr(&c->err, kErrOverflow);
+      for (int r = 0; r < kEnqRounds; ++r) {           // every lane runs every round (warp-wide fill)
+        const bool has = it_len[r] != 0;
+        uint32_t t0 = 1, t1 = 0;                       // warp tiles starting inside the item
+        if (has) {
+          Item it;
+          it.seg_begin = it_seg[r];
+          it.off = off;
+          s.items[idx] = it;
+          s.imask[idx] = uint16_t(it_msk[r]);
+          t0 = (off + kWarpTile - 1) / kWarpTile;
+          t1 = (off + it_len[r] - 1) / kWarpTile;
         }
-        ++idx;
-        off += it_len[r];
+        const bool big = t0 + 2 <= t1;                 // three or more tiles: filled by the warp
+        if (!big) {
+          for (uint32_t t = t0; t <= t1; ++t) {
+            if (t < s.tile_cap) s.tile_first[t] = idx; else atomicOr(&c->err, kErrOverflow);
+          }
+        }
+        for (unsigned bb = __ballot_sync(0xffffffffu, big); bb; bb &= bb - 1) {
+          const int src = __ffs(int(bb)) - 1;
+          const uint32_t f0 = __shfl_sync(0xffffffffu, t0, src), f1 = __shfl_sync(0xffffffffu, t1, src);
+          const uint32_t fi = __shfl_sync(0xffffffffu, idx, src);
+          for (uint32_t t = f0 + lane; t <= f1; t += 32u) {
+            if (t < s.tile_cap) s.tile_first[t] = fi; else atomicOr(&c->err, kErrOverflow);
+          }
+        }
+        if (has) {
+          ++idx;
+          off += it_len[r];
+        }
       }
     }
     __syncthreads();
@@ -889,60 +911,75 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     c->ulist_n = 0;
     c->nvc = 0;
     c->topk_done = 0;
+    for (int j = 0; j < kMaxCols; ++j) c->rec_n[j] = 0;
   }
 }
 
 // ---------------------------------------------------------------- recovery
-// Recovering phase (Algorithm 2) for all selected CGs at once.  Block j of
-// k_recover_cols handles central column j: a backward sweep from the CG nodes,
-// level by level downwards, follows the edges n -> q with h_q = max(a, h_n) + 1
-// (tight, Lemma 3) whose source n was still expanding at level max(a, h_n)
-// (it had not stopped earlier).  Each node carries a bit mask of the CGs it
-// belongs to, OR-ed along the tight edges; the masks of all columns are
-// OR-ed into one union mask (V^c per CG).  k_recover_vc then keeps the nodes
-// of V^c that hold a central keyword: V_C of each CG.
-__global__ void __launch_bounds__(kRecThreads)
+// Recovering phase (Algorithm 2) for all selected CGs at once.  Central
+// column j is swept by one thread-block cluster of kRecCluster CTAs: a
+// backward sweep from the CG nodes, level by level downwards, follows the
+// edges n -> q with h_q = max(a, h_n) + 1 (tight, Lemma 3) whose source n was
+// still expanding at level max(a, h_n) (it had not stopped earlier).  Each
+// node carries a bit mask of the CGs it belongs to, OR-ed along the tight
+// edges; the masks of all columns are OR-ed into one union mask (V^c per
+// CG).  Every CTA of the cluster scans the level's node list (the same block
+// scan of segment lengths), and the CSR entries are dealt round-robin over
+// the cluster, so a hub's row is read by all of its CTAs at once; a cluster
+// barrier separates the levels.  The node list and its counter live in
+// global memory, read through L2 (__ldcg) because other CTAs append to it.
+// k_recover_vc then keeps the nodes of V^c that hold a central keyword: V_C
+// of each CG.
+__global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads)
 k_recover_cols(DevKG g, DevSlot s) {
+  cg::cluster_group cluster = cg::this_cluster();
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   const uint32_t nsel = c->nsel;
-  const int j = blockIdx.x;
-  if (nsel == 0 || j >= q.n_c) return;
+  const int j = int(blockIdx.x / kRecCluster);
+  const uint32_t rank = cluster.block_rank();
+  if (nsel == 0 || j >= q.n_c) return;                     // the same in every CTA of the cluster
   const int maxlev = c->levels[0];
   unsigned long long* rmask = s.rmask + size_t(j) * s.cap;
   uint32_t* rlist = s.rlist + size_t(j) * s.cap;
+  uint32_t* rn = &c->rec_n[j];
   __shared__ uint32_t s_off[kRecThreads];
   __shared__ uint32_t s_rb[kRecThreads];
   __shared__ unsigned long long s_m[kRecThreads];
   __shared__ uint64_t s_warp[33];
-  __shared__ uint32_t s_n, s_cnt, s_total;
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
-    const uint32_t v = uint32_t(c->sel[gi]);
-    if (j == 0) {                                  // the CG nodes themselves belong to V^c
-      const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
-      if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+  __shared__ uint32_t s_total;
+  auto append = [&](uint32_t v, unsigned long long m) {
+    const unsigned long long old = atomicOr(&rmask[v], m);
+    if (old == 0) {
+      const uint32_t p = atomicAdd(rn, 1u);
+      if (p < s.cap) rlist[p] = v; else atomicOr(&c->err, kErrOverflow);
     }
-    if (s.H[size_t(j) * s.hp + v] == 0) continue;   // the CG node holds keyword j
-    const unsigned long long old = atomicOr(&rmask[v], 1ull << gi);
-    if (old == 0) rlist[atomicAdd(&s_n, 1u)] = v;
+  };
+  if (rank == 0) {
+    for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
+      const uint32_t v = uint32_t(c->sel[gi]);
+      if (j == 0) {                                  // the CG nodes themselves belong to V^c
+        const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
+        if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+      }
+      if (s.H[size_t(j) * s.hp + v] == 0) continue;   // the CG node holds keyword j
+      append(v, 1ull << gi);
+    }
   }
-  __syncthreads();
+  cluster.sync();
+  const uint32_t stride = kRecCluster * blockDim.x;
   for (int x = maxlev; x >= 1; --x) {
-    if (threadIdx.x == 0) s_cnt = min(s_n, s.cap);
-    __syncthreads();
-    const uint32_t cnt = s_cnt;
+    const uint32_t cnt = min(__ldcg(rn), s.cap);
     for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
       const uint32_t i = c0 + threadIdx.x;
       uint32_t len = 0, rb = 0;
       unsigned long long m = 0;
       if (i < cnt) {
-        const uint32_t qn = rlist[i];
+        const uint32_t qn = __ldcg(rlist + i);
         if (s.H[size_t(j) * s.hp + qn] == uint8_t(x)) {
           rb = g.row_ptr[qn];
           len = seg_at(g, qn, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
-          m = rmask[qn];
+          m = __ldcg(rmask + qn);
         }
       }
       uint64_t tot = 0;
@@ -951,7 +988,7 @@ k_recover_cols(DevKG g, DevSlot s) {
       if (threadIdx.x == 0) s_total = uint32_t(tot);
       __syncthreads();
       const uint32_t total = s_total;
-      for (uint32_t u = threadIdx.x; u < total; u += blockDim.x) {
+      for (uint32_t u = rank * blockDim.x + threadIdx.x; u < total; u += stride) {
         uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u
         while (lo < hi) {
           const uint32_t mid = lo + ((hi - lo + 1) >> 1);
@@ -964,20 +1001,17 @@ k_recover_cols(DevKG g, DevSlot s) {
         const uint32_t lam = a > hn ? a : hn;
         if (lam + 1 != uint32_t(x)) continue;                               // not tight
         if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
-        const unsigned long long old = atomicOr(&rmask[nb], s_m[lo]);
-        if (old == 0) {
-          const uint32_t p = atomicAdd(&s_n, 1u);
-          if (p < s.cap) rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
-        }
+        append(nb, s_m[lo]);
       }
       __syncthreads();
     }
+    cluster.sync();                                  // level x done everywhere before level x-1
   }
   // fold column j into the union masks and clear the column masks
-  const uint32_t nr = min(s_n, s.cap);
-  for (uint32_t i = threadIdx.x; i < nr; i += blockDim.x) {
-    const uint32_t v = rlist[i];
-    const unsigned long long m = rmask[v];
+  const uint32_t nr = min(__ldcg(rn), s.cap);
+  for (uint32_t i = rank * blockDim.x + threadIdx.x; i < nr; i += stride) {
+    const uint32_t v = __ldcg(rlist + i);
+    const unsigned long long m = __ldcg(rmask + v);
     rmask[v] = 0;
     const unsigned long long old = atomicOr(&s.vmask[v], m);
     if (old == 0) {
@@ -1138,7 +1172,7 @@ void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream
   });
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
-      k_recover_cols<<<kMaxCols, kRecThreads, 0, st>>>(g, s);
+      k_recover_cols<<<kMaxCols * kRecCluster, kRecThreads, 0, st>>>(g, s);
       k_recover_vc<<<sms, 256, 0, st>>>(s);
     });
   }
@@ -1176,7 +1210,7 @@ int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st
 int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
-      k_recover_cols<<<kMaxCols, kRecThreads, 0, st>>>(g, s);
+      k_recover_cols<<<kMaxCols * kRecCluster, kRecThreads, 0, st>>>(g, s);
       k_recover_vc<<<num_sms(), 256, 0, st>>>(s);
     });
     launch_run_setup(g, s, 1, st, prof);
