@@ -95,6 +95,8 @@ struct Ctl {
   unsigned long long e_act_skip;   // E_act of skipped expansions
   uint32_t qlog_n;             // entries of the frontier log (trace mode)
   uint32_t ncg;                // CGs identified (central run)
+  uint32_t ncg_at;             // ncg after the last expanded level
+  uint32_t cg_next[2];         // nodes the expansion of the previous level completed, per level parity
   uint32_t err;                // DevErr bits
   uint32_t n_items, n_work;    // expansion list of the current level
   uint32_t nsel;               // selected CGs

@@ -108,6 +108,8 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->level = 0;
   c->eact_lvl[0] = c->eact_lvl[1] = 0;
   c->skip_lvl = 0;
+  c->ncg_at = 0;
+  c->cg_next[0] = c->cg_next[1] = 0;
   c->tgt_n = c->tgt_done = 0;
   s.bar[0] = 0;                      // barrier arrivals of the persistent kernel
   c->last_expanded = -1;
@@ -269,6 +271,11 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
     }
   }
 
+  // Central run: when the CGs found so far plus the nodes the last expansion
+  // completed reach w, the run stops at this level, so the level only needs
+  // its identification: no work items, no retained frontier.
+  const bool ident_only = run == 0 && ldx<P>(&c->ncg_at) + ldx<P>(&c->cg_next[p]) >= uint32_t(q.w);
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->cg_next[p ^ 1] = 0;   // counted by k_expand of this level
   const uint32_t fq_n = ldx<P>(&c->fq_n[p]);
   const bool sparse = ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && fq_n <= s.fq_limit;
   // The next level's queue is kept only while this level is sparse (a dense
@@ -323,7 +330,12 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       // every load of the node first (they are independent), then the logic
       uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
       uint32_t hv[kMaxCols];
-      if (has) {
+      if (has && ident_only) {
+        cfw = ldx<P>(s.cf + (v >> 5));
+        vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
+#pragma unroll
+        for (int j = 0; j < kMaxCols; ++j) hv[j] = l;   // a node completed at this level has max h = l
+      } else if (has) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
         rb = g.row_ptr[v];
@@ -352,7 +364,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
             if (mx != l) atomicOr(&c->err, kErrInternal);
           }
         } else {
-          expand = true;
+          expand = !ident_only;
         }
       }
       const unsigned cgb = __ballot_sync(0xffffffffu, is_cg);
@@ -618,6 +630,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       if (in_graph) cudaGraphSetConditional(loop, 0);
     } else {
       c->e_act[run] += ea;
+      c->ncg_at = c->ncg;                            // CGs through level l (read by the next enqueue)
       if (skip) {
         c->e_act_skip += ea;
       } else {
@@ -647,7 +660,8 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t ntiles = (n_work + kWarpTile - 1) / kWarpTile;
-  uint64_t hits = 0;
+  uint64_t hits = 0, completed = 0;                  // completed: nodes that now hold every central column
+  const uint32_t fullc = run == 0 ? (1u << q.n_c) - 1u : 0x100u;
   for (uint32_t t = gw; t < ntiles; t += nwarps) {
     const uint32_t t0 = t * kWarpTile;
     const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
@@ -713,12 +727,16 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
           atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
         }
         hits += __popc(won);
+        const uint32_t ob = (old_r[r] >> ((nb & 3u) * 8u)) & 0xffu;
+        completed += ((ob | won) & fullc) == fullc;     // exactly one writer completes a node
       }
       queue_push(s, c, p ^ 1, use_next, fresh, nb);
     }
   }
-  const uint64_t th = block_sum(hits, s_warp);
+  const uint64_t hc = block_sum(hits | (completed << 40), s_warp);   // both counts in one reduction
+  const uint64_t th = hc & ((1ull << 40) - 1ull), tc = hc >> 40;
   if (threadIdx.x == 0 && th) atomicAdd(&c->hits[run], (unsigned long long)th);
+  if (threadIdx.x == 0 && tc) atomicAdd(&c->cg_next[p ^ 1], uint32_t(tc));
   return false;
 }
 
