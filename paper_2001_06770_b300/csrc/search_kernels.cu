@@ -452,7 +452,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   if (threadIdx.x == 0 && et) atomicAdd(&c->eact_lvl[p], (unsigned long long)et);
 }
 
-__global__ void __launch_bounds__(kEnqThreads)
+__global__ void __launch_bounds__(kEnqThreads, 5)      // at most 51 registers: 5 blocks per SM
 k_enqueue(DevKG g, DevSlot s, int run) {
   Ctl* c = s.ctl;
   if (c->done) return;
