@@ -138,6 +138,19 @@ def allmax(ws, x: float) -> float:
     return float(t.item())
 
 
+def host_cpu() -> dict:
+    """Host cores and CPU model (the oracle and RAKS-CPU run there)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def oracle_sample(ds, qs, n, act=None, budget_s=20.0):
     """Serial oracle on the first n queries, stopping early once budget_s
     seconds are spent (at least one query): (queries/s, seconds, queries)."""
@@ -271,8 +284,11 @@ def expand_roofline(kg, qs, stats):
     peak, peak_kind = hbm_peak()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == expand_source_sha() else None
     total_ms = sum(v[0] for v in prof.values())
+    avg_s = exp_ms / 1e3 / max(exp_launches, 1)
+    dram_gbs = traffic / avg_s / 1e9 if traffic and avg_s > 0 else None
     roof = {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
             "alg_bytes_per_launch": alg_bytes / max(exp_launches, 1),
             "avg_launch_us": 1e3 * exp_ms / max(exp_launches, 1), "launches": exp_launches,
             "share_of_device_time": exp_ms / total_ms if total_ms else None}
@@ -417,6 +433,7 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
                          if par else
                          {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                           "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"}),
+        "host_cpu": host_cpu(),
         "cpu_baseline_one_core": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                                   "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
         "raks_cpu": None if mc is None else {
