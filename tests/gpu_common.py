@@ -64,3 +64,36 @@ def dataset_queries(name, ds, n, seed=3):
                                max_depth=7, seed=seed, head_min=int(np.diff(ds.kw_ptr).max() // 4),
                                tail_max=20)
     return qs
+
+
+def check_levels(g, adj, H, stop, last_expanded, postings, rng, n_sample=4000, nodes=None):
+    """Fixed-point property of the hit levels (Theorem 5 with the stop rules)
+    on sampled nodes and up to 300 nodes of each keyword's postings, or on
+    `nodes`: h = 0 exactly on keyword nodes; h > 0 is one more than the
+    smallest max(h_u, a) over neighbours u that expanded to the node (reached,
+    not stopped by then, at a level <= last_expanded); an unreached node has
+    no such neighbour.  `adj` holds the device's packed rows (a << 26 | u)."""
+    rp = g.row_ptr
+    if nodes is None:
+        picks = [rng.choice(np.asarray(p), size=min(len(p), 300), replace=False) for p in postings if len(p)]
+        nodes = np.unique(np.concatenate([rng.integers(0, g.n, size=n_sample)] + picks))
+    for j in range(H.shape[1]):
+        kw = set(int(x) for x in postings[j])
+        h = H[:, j].astype(np.int64)
+        for v in nodes:
+            v = int(v)
+            row = adj[rp[v]:rp[v + 1]]
+            a = (row >> 26).astype(np.int64)
+            u = (row & ((1 << 26) - 1)).astype(np.int64)
+            hu = h[u]
+            lam = np.maximum(hu, a)
+            live = (hu != INF) & (lam < stop[u]) & (lam <= last_expanded)   # u expanded to v at level lam
+            hv = int(h[v])
+            if v in kw:
+                assert hv == 0
+                continue
+            assert hv != 0
+            if hv == INF:
+                assert not live.any(), f"node {v} column {j}: reachable but unreached"
+            else:
+                assert live.any() and int((lam[live] + 1).min()) == hv, f"node {v} column {j}: level {hv}"
