@@ -69,8 +69,10 @@ def test_large_trace_properties(large):
 
 
 def test_large_paths_agree(large):
+    """One-at-a-time queries and the mixed shapes of the batched workload
+    (|C| 2-6, |M| 0-8, head and tail keywords, k in {5, 10, 20})."""
     ds, kg, adj, qs = large
-    sample = [qs[i] for i in (0, 1, 2, 3)]
+    sample = [qs[i] for i in (0, 1, 2, 3)] + rpqgen.workload_queries("batched", ds)[:6]
     batch = kg.search_batch(sample)
     for q, (bres, _, status) in zip(sample, batch):
         assert status == 0
