@@ -103,10 +103,19 @@ int create_slot(rpq_kg* kg, Slot** out) {
 #define SA(ptr, bytes) do { if (rc == RPQ_OK) rc = A((void**)&(ptr), (bytes)); } while (0)
   d.hp = uint32_t((n + 15) / 16 * 16);
   SA(d.H, size_t(d.hp) * kMaxCols + 16);
-  SA(d.vis, ((n + 3) / 4) * 4 + 16);
-  SA(d.F[0], nwords * 4 + 16);
-  SA(d.F[1], nwords * 4 + 16);
-  SA(d.cf, nwords * 4 + 16);
+  {   // per-run state cleared by one memset: visited bytes, F[0], F[1], cf
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t vb = up(((n + 3) / 4) * 4 + 16), fb = up(nwords * 4 + 16);
+    d.run_clear_bytes = vb + 3 * fb;
+    SA(d.run_clear, d.run_clear_bytes);
+    if (rc == RPQ_OK) {
+      char* b = static_cast<char*>(d.run_clear);
+      d.vis = reinterpret_cast<uint32_t*>(b);
+      d.F[0] = reinterpret_cast<uint32_t*>(b + vb);
+      d.F[1] = reinterpret_cast<uint32_t*>(b + vb + fb);
+      d.cf = reinterpret_cast<uint32_t*>(b + vb + 2 * fb);
+    }
+  }
   SA(d.stopl, n + 16);
   SA(d.items, sizeof(Item) * d.cap);
   SA(d.imask, sizeof(uint16_t) * d.cap + 16);

@@ -148,6 +148,8 @@ struct DevSlot {
   uint32_t tgt_cap;
   uint32_t target;            // marginal run: check V_C first and skip a final expansion
   uint32_t tgt_min_work;      // ... on levels with at least this many work units
+  void* run_clear;            // vis, F[0], F[1], cf in one block, cleared per run
+  unsigned long long run_clear_bytes;
   uint32_t* sticky;           // device error bits kept across queries
   unsigned* bar;              // grid barrier of the persistent run kernel: count, generation
   uint32_t persistent;        // run each level loop as one cooperative k_run launch

@@ -1130,13 +1130,9 @@ int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw
 
 // Reset and seed one run.
 void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof) {
-  const size_t nwords = (size_t(g.n) + 31) / 32;
   timed(prof, RPQ_PROF_SETUP, st, [&] {
     k_run_start<<<1, 32, 0, st>>>(s, run);
-    cudaMemsetAsync(s.vis, 0, ((size_t(g.n) + 3) / 4) * 4, st);
-    cudaMemsetAsync(s.F[0], 0, nwords * 4, st);
-    cudaMemsetAsync(s.F[1], 0, nwords * 4, st);
-    cudaMemsetAsync(s.cf, 0, nwords * 4, st);
+    cudaMemsetAsync(s.run_clear, 0, s.run_clear_bytes, st);   // visited bytes, F[0], F[1], cf
     k_seed<<<num_sms() * 2, 256, 0, st>>>(g, s, run);
   });
 }
