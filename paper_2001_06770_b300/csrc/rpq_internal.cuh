@@ -110,6 +110,7 @@ struct Ctl {
   uint32_t n_res;
   uint32_t topk_done;          // k_topk: blocks finished
   uint32_t rec_n[kMaxCols];    // recovery: node list length per central column
+  uint32_t rec_done;           // recovery: CTAs finished
   unsigned long long e_act[2];  // per run
   unsigned long long hits[2];
   unsigned long long units, items, frontier;  // work totals of both runs

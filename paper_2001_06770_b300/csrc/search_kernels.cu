@@ -3,7 +3,8 @@
 // One query runs as a sequence of launches on the slot's stream:
 //   k_set_query                       copy parameters, reset the control block
 //   per run (central, then marginal):
-//     k_run_start, memsets of vis / F / cf, k_seed (Section 4.2.1)
+//     k_run_start (marginal run; k_set_query prepares the central one), one
+//     memset of vis / F / cf, k_seed (Section 4.2.1)
 //     per Glevel l:  k_enqueue        frontier enqueue + reset (4.2.2) and
 //                                     result identification (4.2.3,
 //                                     Theorem 3; PTC stop; RPG match;
@@ -13,7 +14,7 @@
 //                    k_expand         termination decision + expansion
 //                                     (Algorithm 1) of the newly active edges
 //   after the central run: k_topk (top-w CGs),
-//                          k_recover_cols, k_recover_vc (Algorithm 2 -> V_C)
+//                          k_recover_cols (Algorithm 2 -> V_C)
 //   at the end:            k_results (Eq. 6, top-k by (S^r, id))
 // The Glevel is kept in the control block, so the level kernels form the body
 // of a CUDA-graph WHILE node that k_expand ends when the run stops, or the
@@ -91,6 +92,8 @@ __global__ void k_set_query(DevSlot s, QueryDev qv, const int32_t* d_kw) {
   for (size_t i = 0; i < sizeof(Ctl) / 4; ++i) w[i] = 0;
   c->levels[0] = c->levels[1] = -1;
   c->last_expanded = -1;
+  c->fq_use[0] = 1;                  // the rest of k_run_start's state for the central run
+  s.bar[0] = 0;
   *s.n_res = 0;
 }
 
@@ -946,8 +949,8 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
 // the cluster, so a hub's row is read by all of its CTAs at once; a cluster
 // barrier separates the levels.  The node list and its counter live in
 // global memory, read through L2 (__ldcg) because other CTAs append to it.
-// k_recover_vc then keeps the nodes of V^c that hold a central keyword: V_C
-// of each CG.
+// The last CTA to finish then keeps the nodes of V^c that hold a central
+// keyword: V_C of each CG.
 __global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads)
 k_recover_cols(DevKG g, DevSlot s) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -1037,19 +1040,25 @@ k_recover_cols(DevKG g, DevSlot s) {
       if (p < s.cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
     }
   }
-}
-
-__global__ void k_recover_vc(DevSlot s) {
-  Ctl* c = s.ctl;
-  const int nc = s.q->n_c;
-  const uint32_t nu = min(c->ulist_n, s.cap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
-    const uint32_t v = s.ulist[i];
-    unsigned long long m = s.vmask[v];
+  // the last CTA of all columns keeps the nodes of V^c that hold a central
+  // keyword: V_C of each CG, as (g << 26 | node) pairs
+  __shared__ uint32_t s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&c->rec_done, 1u) == uint32_t(q.n_c) * kRecCluster - 1u ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t nu = min(__ldcg(&c->ulist_n), s.cap);
+  for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) {
+    const uint32_t v = __ldcg(s.ulist + i);
+    unsigned long long m = __ldcg(s.vmask + v);
     s.vmask[v] = 0;
     const uint32_t vb = vis_byte(s.vis, v);
     bool holds = false;
-    for (int j = 0; j < nc; ++j) holds |= ((vb >> j) & 1u) && s.H[size_t(j) * s.hp + v] == 0;
+    for (int jj = 0; jj < q.n_c; ++jj) holds |= ((vb >> jj) & 1u) && s.H[size_t(jj) * s.hp + v] == 0;
     if (!holds) continue;
     for (; m; m &= m - 1) {
       const uint32_t gi = __ffsll(m) - 1;
@@ -1057,6 +1066,7 @@ __global__ void k_recover_vc(DevSlot s) {
       if (p < s.cap) s.vcl[p] = (gi << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
     }
   }
+  if (threadIdx.x == 0) c->rec_done = 0;
 }
 
 // --------------------------------------------------------------- results
@@ -1131,7 +1141,7 @@ int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw
 // Reset and seed one run.
 void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof) {
   timed(prof, RPQ_PROF_SETUP, st, [&] {
-    k_run_start<<<1, 32, 0, st>>>(s, run);
+    if (run != 0) k_run_start<<<1, 32, 0, st>>>(s, run);      // k_set_query prepared the central run
     cudaMemsetAsync(s.run_clear, 0, s.run_clear_bytes, st);   // visited bytes, F[0], F[1], cf
     k_seed<<<num_sms() * 2, 256, 0, st>>>(g, s, run);
   });
@@ -1187,7 +1197,6 @@ void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
       k_recover_cols<<<kMaxCols * kRecCluster, kRecThreads, 0, st>>>(g, s);
-      k_recover_vc<<<sms, 256, 0, st>>>(s);
     });
   }
 }
@@ -1225,7 +1234,6 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
       k_recover_cols<<<kMaxCols * kRecCluster, kRecThreads, 0, st>>>(g, s);
-      k_recover_vc<<<num_sms(), 256, 0, st>>>(s);
     });
     launch_run_setup(g, s, 1, st, prof);
     for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
@@ -1237,8 +1245,8 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
 // Kernels launched by one query in a graph (for launch accounting): fixed
 // kernels plus, per run, two per executed Glevel or one persistent launch.
 int kernels_fixed_per_query(int n_m) {
-  const int run = 2;                                // k_run_start, k_seed
-  return 1 + run + 1 + (n_m > 0 ? 2 + run : 0) + 1;
+  // k_set_query, k_seed, k_topk, [k_recover_cols, k_run_start, k_seed], k_results
+  return 1 + 1 + 1 + (n_m > 0 ? 3 : 0) + 1;
 }
 
 }  // namespace rpq

@@ -608,9 +608,11 @@ static int enqueue_search(rpq_kg* kg, Slot* s, const QueryDev& qv, const SgDev& 
   k_sg_rank<<<1, kMaxK, 0, st>>>(d, sg);
   k_sg_count<<<sms, kSgThreads, 0, st>>>(sg);
   k_sg_offsets<<<1, 32, 0, st>>>(d, sg);
-  const int levels = 2 * (qv.L + 1);            // k_enqueue + k_expand per Glevel
-  const int run = 2;                            // k_run_start, k_seed
-  return 1 + run + levels + 5 + 4 + (qv.n_m > 0 ? run + levels + 4 : 0) + 1 + 3;
+  // k_set_query, k_seed, levels (k_enqueue, k_expand; + k_target in the
+  // marginal run), k_topk, 4 recovery passes, [k_run_start, k_seed, levels,
+  // 4 recovery passes], k_results, k_sg_rank/count/offsets
+  const int levels = qv.L + 1;
+  return 1 + 1 + 2 * levels + 1 + 4 + (qv.n_m > 0 ? 2 + 3 * levels + 4 : 0) + 1 + 3;
 }
 
 }  // namespace rpq
