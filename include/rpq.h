@@ -308,7 +308,8 @@ int rpq_sync_device(rpq_kg *kg);
  *   next_queue_mult       the next level's queue is kept while the current
  *                         level's work (CSR entries) is at most
  *                         next_queue_mult x that limit (default 16)
- *   batch_slots           concurrent search slots of rpq_search_batch (8)
+ *   batch_slots           concurrent search slots of rpq_search_batch (8; fewer
+ *                         when device memory for more is not available)
  *   flat_levels           Glevels per run replayed as plain CUDA-graph nodes;
  *                         the rest run in a WHILE node that a run stopping
  *                         earlier never enters (4; 0 = all levels in the
@@ -326,7 +327,7 @@ int rpq_set_tuning(rpq_kg *kg, const rpq_tuning *t);
 /* Autotuner: times the one-at-a-time search of the nq sample queries for each
  * queue_div in {8, 32, 128} x next_queue_mult in {4, 16, 64}, then for
  * flat_levels in {2, 3, 4, 6, 64}, then rpq_search_batch for batch_slots in
- * {4, 8, 16}, keeps the fastest setting
+ * {4, 8, 16, 32}, keeps the fastest setting
  * (the median of `repeats` timed passes after one warm-up pass decides) and
  * returns it in *best (may be NULL).  Results are the same under every
  * setting. */

@@ -529,10 +529,15 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
                      int32_t* status, rpq_stats* stats) {
   if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
-  const int nslots = std::max(1, std::min<int>(slot_count(kg), nq));
+  int nslots = std::max(1, std::min<int>(slot_count(kg), nq));
   std::vector<Slot*> slots(size_t(nslots), nullptr);
   for (int i = 0; i < nslots; ++i) {          // slots 1..nslots: slot 0 serves single searches
     const int rc = get_slot(kg, size_t(i) + 1, &slots[size_t(i)]);
+    if (rc == RPQ_ENOMEM && i > 0) {          // device memory for fewer slots only: use those
+      nslots = i;
+      slots.resize(size_t(i));
+      break;
+    }
     if (rc != RPQ_OK) return rc;
   }
   std::vector<int64_t> base(size_t(nq) + 1, 0);
@@ -763,7 +768,7 @@ int rpq_autotune(rpq_kg* kg, const rpq_query* qs, int32_t nq, int32_t repeats, r
   }
   cur = bestt;
   best_s = 1e30;
-  for (int bs : {4, 8, 16}) {
+  for (int bs : {4, 8, 16, 32}) {
     cur.batch_slots = bs;
     if ((rc = rpq_set_tuning(kg, &cur)) != RPQ_OK) return rc;
     double sec = 0;
