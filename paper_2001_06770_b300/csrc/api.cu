@@ -311,7 +311,7 @@ static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, int L, int K, cudaGra
 static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
   if (!use_graphs() || kg->prof) {
     RPQ_CUDA(cudaGetLastError());
-    return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof);
+    return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof, true);
   }
   (void)n_c;
   const int K = s->d.persistent ? L + 1 : flat_levels(kg, L);
@@ -325,7 +325,7 @@ static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
     } else {                                            // one persistent kernel per run
       cudaGraph_t graph = nullptr;
       RPQ_CUDA(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-      const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr);
+      const int rc = launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr, false);
       const cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
       if (rc != RPQ_OK || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

@@ -108,7 +108,8 @@ void free_subgraph_scratch(rpq_kg* kg);     // subgraph.cu
 
 // Kernel launch sequences (search_kernels.cu).
 int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st);
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof,
+                      bool stop_early);
 void launch_run_setup(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof);
 void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Prof* prof,
                   cudaGraphConditionalHandle loop, bool in_graph);

@@ -1206,15 +1206,30 @@ void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof) {
 }
 
 // The whole query without a graph: one persistent launch or L+1 level pairs per run.
-int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof) {
+// With stop_early (direct launches, never under capture) the host waits after
+// each Glevel and launches no further level once the run has stopped, like a
+// query graph whose run ends inside its plain levels; kernel timings and
+// launch lists then hold no early-exit launches.
+int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof,
+                      bool stop_early) {
+  auto levels = [&](int run) {
+    for (int l = 0; l <= L; ++l) {
+      launch_level(g, s, run, st, prof, 0, false);
+      if (!stop_early) continue;
+      uint32_t done = 0;
+      if (cudaStreamSynchronize(st) != cudaSuccess ||
+          cudaMemcpy(&done, &s.ctl->done, sizeof(done), cudaMemcpyDeviceToHost) != cudaSuccess || done)
+        break;
+    }
+  };
   launch_run_setup(g, s, 0, st, prof);
   if (s.persistent) launch_run_persistent(g, s, 0, st, prof);
-  else for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
+  else levels(0);
   launch_select_recover(g, s, n_m, st, prof);
   if (n_m > 0) {
     launch_run_setup(g, s, 1, st, prof);
     if (s.persistent) launch_run_persistent(g, s, 1, st, prof);
-    else for (int l = 0; l <= L; ++l) launch_level(g, s, 1, st, prof, 0, false);
+    else levels(1);
   }
   launch_results(s, st, prof);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
