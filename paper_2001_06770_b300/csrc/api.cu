@@ -46,15 +46,17 @@ static int flat_levels(const rpq_kg* kg, int L) {
 // Slot parameters that follow the tuning.  Graphs captured with other values
 // are dropped (kernel parameters are baked into them).
 void apply_tuning(rpq_kg* kg, Slot* s) {
-  const size_t n = size_t(kg->dev.n), nwords = (n + 31) / 32;
+  const size_t n = size_t(kg->dev.n);
   const size_t div = size_t(std::max(1, kg->tune.queue_div));
   s->d.fq_limit = uint32_t(std::min<size_t>(s->d.cap, std::max<size_t>(n / div, std::min<size_t>(4096, s->d.cap))));
-  (void)nwords;
   s->d.fq_next_mult = uint32_t(std::max(1, kg->tune.next_queue_mult));
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   s->graphs.clear();
 }
 
+// RPQ_NO_GRAPH=1 launches every kernel directly (for launch lists and
+// per-kernel profiles).  The host then waits after each Glevel to stop at the
+// end of a run, so concurrent slots (batch, server) no longer overlap.
 static bool use_graphs() {
   static int v = -1;
   if (v < 0) { const char* e = getenv("RPQ_NO_GRAPH"); v = (e && *e && *e != '0') ? 0 : 1; }
