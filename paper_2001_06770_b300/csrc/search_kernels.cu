@@ -49,6 +49,7 @@ constexpr int kEnqRounds = 4;
 constexpr int kExpThreads = 256;
 constexpr int kExpRounds = 4;                      // 32-unit rounds per warp tile
 constexpr int kTgtThreads = 256;
+constexpr uint32_t kTgtMaxTasks = 4096;             // (V_C node, column) pairs the V_C check takes on
 constexpr int kWarpTile = 32 * kExpRounds;         // 128 work units per warp tile
 constexpr int kRecThreads = 1024;
 constexpr int kRecCluster = 8;                     // CTAs sweeping one keyword column
@@ -479,8 +480,10 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 // selected CG matched, Theorem 4, or l+1 = L) and some hit was applied (so
 // Q_{l+1} is not empty), nothing else the expansion of level l would compute
 // can reach the results, and k_expand skips it.  Levels with fewer than
-// tgt_min_work work units are left alone (the check would cost more than the
-// expansion).  Off in trace mode, where every frontier is compared.
+// tgt_min_work work units, and queries whose V_C holds more than
+// kTgtMaxTasks (node, column) pairs (keywords on hundreds of thousands of
+// nodes: the single block applying the hits would dominate), are left alone.
+// Off in trace mode, where every frontier is compared.
 __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
   Ctl* c = s.ctl;
   if (c->done || !s.target) return;
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
   // the run ends at level l anyway (the stop test of k_expand), or the level
   // is too small for a skip to pay for the check
   if (nm == 0 || c->nq[p] == 0 || c->n_matched >= nsel || c->rpg_stop || l >= uint32_t(q.L)) return;
-  if ((c->work[p] & kWorkMask) < s.tgt_min_work) return;
+  if ((c->work[p] & kWorkMask) < s.tgt_min_work || min(c->nvc, s.cap) * uint32_t(nm) > kTgtMaxTasks) return;
   const uint32_t nvc = min(c->nvc, s.cap);
   const uint32_t ntask = nvc * uint32_t(nm);
   const uint32_t lane = lane_id();
