@@ -265,9 +265,10 @@ WORKLOADS = {
 }
 
 
-def expand_roofline(kg, qs, stats):
+def expand_roofline(kg, qs, stats, workload="medium"):
     """Profiling pass: device time of each kernel class, and the expansion
-    kernel's algorithmic bytes per second against the measured HBM peak."""
+    kernel's algorithmic bytes per second against the measured HBM peak.  The
+    stored ncu DRAM traffic applies to the medium workload's 64 queries only."""
     kg.set_profiling(True)
     for q in qs:
         kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
@@ -282,7 +283,8 @@ def expand_roofline(kg, qs, stats):
     alg_bytes = 4 * units + e_act + 2 * hits + 10 * items      # adjacency, level checks, writes, items
     achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == expand_source_sha() else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if workload == "medium" and len(qs) == 64 and NCU_TRAFFIC["sha1"] == expand_source_sha() else None)
     total_ms = sum(v[0] for v in prof.values())
     avg_s = exp_ms / 1e3 / max(exp_launches, 1)
     dram_gbs = traffic / avg_s / 1e9 if traffic and avg_s > 0 else None
@@ -406,7 +408,7 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
     t_b = allmax(ws, time.perf_counter() - t0)
     batched = ws * nq * args.steps / t_b
 
-    roof, kms = expand_roofline(kg, qs, stats)
+    roof, kms = expand_roofline(kg, qs, stats, args.workload)
     if rank != 0:
         return None
     cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
@@ -470,7 +472,7 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
     stats = [st for _, st, _ in out]
     e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
     sstats = [stats[i] for i in sample]
-    roof, kms = expand_roofline(kg, [qs[i] for i in sample], sstats)
+    roof, kms = expand_roofline(kg, [qs[i] for i in sample], sstats, args.workload)
     if rank != 0:
         return None
     cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
