@@ -126,6 +126,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
   SA(d.rmask, sizeof(unsigned long long) * d.cap * kMaxCols);
   SA(d.vmask, sizeof(unsigned long long) * d.cap);
   SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
+  SA(d.rcnt, sizeof(uint32_t) * kRecStride * kMaxCols);
   d.tile_cap = uint32_t(uint64_t(kg->m2) / 128 + 2);
   SA(d.tile_first, sizeof(uint32_t) * d.tile_cap);
   SA(d.fq[0], sizeof(uint32_t) * d.cap);         // any queue limit up to n fits
@@ -145,6 +146,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
     // masks start at zero; the recovery kernel restores zero after each use
     if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess ||
         cudaMemset(d.vmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
+        cudaMemset(d.rcnt, 0, sizeof(uint32_t) * kRecStride * kMaxCols) != cudaSuccess ||
         cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
         cudaMemset(d.bar, 0, 16) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||

@@ -30,6 +30,7 @@ constexpr uint8_t kInf = 255;
 constexpr int kMaxCols = 8;
 constexpr int kMaxK = 64;
 constexpr int kMaxLevel = 63;
+constexpr int kRecStride = kMaxLevel + 3;   // recovery counters of one column
 constexpr int kMaxLabels = 8192;
 
 enum DevErr : uint32_t {
@@ -109,7 +110,6 @@ struct Ctl {
   uint32_t fq_use[2];          // the queue of this parity is being filled
   uint32_t n_res;
   uint32_t topk_done;          // k_topk: blocks finished
-  uint32_t rec_n[kMaxCols];    // recovery: node list length per central column
   uint32_t rec_done;           // recovery: CTAs finished
   unsigned long long e_act[2];  // per run
   unsigned long long hits[2];
@@ -134,6 +134,7 @@ struct DevSlot {
   unsigned long long* rmask;  // recovery: per-column CG mask per node (kMaxCols * cap)
   unsigned long long* vmask;  // recovery: union over columns
   uint32_t* rlist;            // recovery: per-column node lists (kMaxCols * cap)
+  uint32_t* rcnt;             // recovery: per-column counters (kMaxCols * kRecStride), zero between uses
   uint32_t* tile_first;       // expansion: first item of each warp tile
   uint32_t tile_cap;
   uint32_t* fq[2];            // frontier queues (nodes of F), per level parity

@@ -935,7 +935,6 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     c->ulist_n = 0;
     c->nvc = 0;
     c->topk_done = 0;
-    for (int j = 0; j < kMaxCols; ++j) c->rec_n[j] = 0;
   }
 }
 
@@ -946,15 +945,25 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
 // edges n -> q with h_q = max(a, h_n) + 1 (tight, Lemma 3) whose source n was
 // still expanding at level max(a, h_n) (it had not stopped earlier).  Each
 // node carries a bit mask of the CGs it belongs to, OR-ed along the tight
-// edges; the masks of all columns are OR-ed into one union mask (V^c per
-// CG).  Every CTA of the cluster scans the level's node list (the same block
-// scan of segment lengths), and the CSR entries are dealt round-robin over
-// the cluster, so a hub's row is read by all of its CTAs at once; a cluster
-// barrier separates the levels.  The node list and its counter live in
-// global memory, read through L2 (__ldcg) because other CTAs append to it.
-// The last CTA to finish then keeps the nodes of V^c that hold a central
-// keyword: V_C of each CG.
-__global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads)
+// edges; a node's mask is final once the level above it is done, since every
+// tight edge into it starts one level higher or more.
+//
+// The column's node list (cap entries) holds each reached node once, filed
+// when it is first reached: a node one level below the node that reached it
+// (the usual case) goes into the segment of that level, the segments growing
+// upwards in order of decreasing level; any other node (a CG node, or one
+// reached over an edge whose activation level exceeds its own h) goes into
+// the overflow part, which grows down from the end.  Level x visits its own
+// segment and the overflow nodes with h = x, not the whole list.  Every CTA
+// of the cluster scans those entries (the same block scan of row lengths) and
+// the CSR entries are dealt round-robin over the cluster, so a hub's row is
+// read by all of its CTAs at once; a cluster barrier separates the levels.
+// The lists and counters live in global memory, read through L2 (__ldcg)
+// because other CTAs append to them.  At the end every reached node that
+// holds a central keyword ORs its column mask into the union mask (vmask),
+// every column mask is cleared, and the last CTA of all columns turns the
+// union masks into V_C of each CG.
+__global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads, 1)
 k_recover_cols(DevKG g, DevSlot s) {
   cg::cluster_group cluster = cg::this_cluster();
   Ctl* c = s.ctl;
@@ -964,20 +973,20 @@ k_recover_cols(DevKG g, DevSlot s) {
   const uint32_t rank = cluster.block_rank();
   if (nsel == 0 || j >= q.n_c) return;                     // the same in every CTA of the cluster
   const int maxlev = c->levels[0];
-  unsigned long long* rmask = s.rmask + size_t(j) * s.cap;
-  uint32_t* rlist = s.rlist + size_t(j) * s.cap;
-  uint32_t* rn = &c->rec_n[j];
+  const uint32_t cap = s.cap;
+  const uint8_t* Hj = s.H + size_t(j) * s.hp;
+  unsigned long long* rmask = s.rmask + size_t(j) * cap;
+  uint32_t* rlist = s.rlist + size_t(j) * cap;
+  uint32_t* sn = s.rcnt + size_t(j) * kRecStride;          // sn[y]: segment length of level y
+  uint32_t* ovf = sn + (kMaxLevel + 2);                    // overflow length
   __shared__ uint32_t s_off[kRecThreads];
   __shared__ uint32_t s_rb[kRecThreads];
   __shared__ unsigned long long s_m[kRecThreads];
   __shared__ uint64_t s_warp[33];
   __shared__ uint32_t s_total;
-  auto append = [&](uint32_t v, unsigned long long m) {
-    const unsigned long long old = atomicOr(&rmask[v], m);
-    if (old == 0) {
-      const uint32_t p = atomicAdd(rn, 1u);
-      if (p < s.cap) rlist[p] = v; else atomicOr(&c->err, kErrOverflow);
-    }
+  auto to_overflow = [&](uint32_t v) {
+    const uint32_t p = atomicAdd(ovf, 1u);
+    if (p < cap) rlist[cap - 1u - p] = v; else atomicOr(&c->err, kErrOverflow);
   };
   if (rank == 0) {
     for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
@@ -986,21 +995,23 @@ k_recover_cols(DevKG g, DevSlot s) {
         const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
         if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
       }
-      if (s.H[size_t(j) * s.hp + v] == 0) continue;   // the CG node holds keyword j
-      append(v, 1ull << gi);
+      if (Hj[v] == 0) continue;                      // the CG node holds keyword j
+      if (atomicOr(&rmask[v], 1ull << gi) == 0) to_overflow(v);
     }
   }
   cluster.sync();
   const uint32_t stride = kRecCluster * blockDim.x;
+  uint32_t base = 0;                                 // first entry of the segment of level x
   for (int x = maxlev; x >= 1; --x) {
-    const uint32_t cnt = min(__ldcg(rn), s.cap);
+    const uint32_t nseg = __ldcg(&sn[x]), nov = min(__ldcg(ovf), cap);
+    const uint32_t next_base = base + nseg, cnt = nseg + nov;
     for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
       const uint32_t i = c0 + threadIdx.x;
       uint32_t len = 0, rb = 0;
       unsigned long long m = 0;
       if (i < cnt) {
-        const uint32_t qn = __ldcg(rlist + i);
-        if (s.H[size_t(j) * s.hp + qn] == uint8_t(x)) {
+        const uint32_t qn = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
+        if (i < nseg || Hj[qn] == uint8_t(x)) {
           rb = g.row_ptr[qn];
           len = seg_at(g, qn, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
           m = __ldcg(rmask + qn);
@@ -1021,30 +1032,43 @@ k_recover_cols(DevKG g, DevSlot s) {
         const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
         const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
         if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
-        const uint32_t hn = s.H[size_t(j) * s.hp + nb];
+        const uint32_t hn = Hj[nb];
         const uint32_t lam = a > hn ? a : hn;
         if (lam + 1 != uint32_t(x)) continue;                               // not tight
         if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
-        append(nb, s_m[lo]);
+        if (atomicOr(&rmask[nb], s_m[lo]) != 0) continue;                  // already listed
+        if (hn + 1 == uint32_t(x)) {
+          const uint32_t p = next_base + atomicAdd(&sn[hn], 1u);
+          if (p < cap) rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
+        } else {
+          to_overflow(nb);
+        }
       }
       __syncthreads();
     }
     cluster.sync();                                  // level x done everywhere before level x-1
+    base = next_base;
   }
-  // fold column j into the union masks and clear the column masks
-  const uint32_t nr = min(__ldcg(rn), s.cap);
-  for (uint32_t i = rank * blockDim.x + threadIdx.x; i < nr; i += stride) {
-    const uint32_t v = __ldcg(rlist + i);
+  // every reached node: a keyword holder's column mask goes into the union
+  // mask; the column mask is cleared
+  const uint32_t nseg = base + __ldcg(&sn[0]), nov = min(__ldcg(ovf), cap);
+  for (uint32_t i = rank * blockDim.x + threadIdx.x; i < nseg + nov; i += stride) {
+    const uint32_t v = i < nseg ? __ldcg(rlist + i) : __ldcg(rlist + cap - 1u - (i - nseg));
     const unsigned long long m = __ldcg(rmask + v);
     rmask[v] = 0;
+    const uint32_t vb = vis_byte(s.vis, v);
+    bool holds = false;
+    for (int jj = 0; jj < q.n_c; ++jj) holds |= ((vb >> jj) & 1u) && s.H[size_t(jj) * s.hp + v] == 0;
+    if (!holds) continue;
     const unsigned long long old = atomicOr(&s.vmask[v], m);
     if (old == 0) {
       const uint32_t p = atomicAdd(&c->ulist_n, 1u);
-      if (p < s.cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
+      if (p < cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
     }
   }
   // the last CTA of all columns keeps the nodes of V^c that hold a central
-  // keyword: V_C of each CG, as (g << 26 | node) pairs
+  // keyword: V_C of each CG, as (g << 26 | node) pairs; it also clears the
+  // list counters
   __shared__ uint32_t s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1054,7 +1078,8 @@ k_recover_cols(DevKG g, DevSlot s) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const uint32_t nu = min(__ldcg(&c->ulist_n), s.cap);
+  for (uint32_t i = threadIdx.x; i < uint32_t(q.n_c) * kRecStride; i += blockDim.x) s.rcnt[i] = 0;
+  const uint32_t nu = min(__ldcg(&c->ulist_n), cap);
   for (uint32_t i = threadIdx.x; i < nu; i += blockDim.x) {
     const uint32_t v = __ldcg(s.ulist + i);
     unsigned long long m = __ldcg(s.vmask + v);
@@ -1066,7 +1091,7 @@ k_recover_cols(DevKG g, DevSlot s) {
     for (; m; m &= m - 1) {
       const uint32_t gi = __ffsll(m) - 1;
       const uint32_t p = atomicAdd(&c->nvc, 1u);
-      if (p < s.cap) s.vcl[p] = (gi << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
+      if (p < cap) s.vcl[p] = (gi << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
     }
   }
   if (threadIdx.x == 0) c->rec_done = 0;
