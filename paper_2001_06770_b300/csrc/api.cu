@@ -481,6 +481,7 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
   kg->dev.adj = kg->d_adj;
   kg->dev.amax = kg->d_amax;
   kg->dev.lvx = kg->d_lvx;
+  kg->dev.lvx_long = kg->d_lvx_long;
   kg->dev.n_kw = d->n_kw;
   kg->dev.kw_ptr = kg->d_kw_ptr;
   kg->dev.kw_nodes = kg->d_kw_nodes;
@@ -493,7 +494,7 @@ int rpq_free_kg(rpq_kg* kg) {
   for (Slot* s : kg->slots) destroy_slot(s);
   free_subgraph_scratch(kg);
   delete kg->prof;
-  cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax); cudaFree(kg->d_lvx);
+  cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax); cudaFree(kg->d_lvx); cudaFree(kg->d_lvx_long);
   cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);
   delete kg;
   return RPQ_OK;

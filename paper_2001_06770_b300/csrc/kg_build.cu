@@ -234,14 +234,29 @@ k_sort_large(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __
   }
 }
 
-// Level index of each row (see kLvxLevels): one thread per row.
+// Level index of each row (see kLvxLevels): one thread per row; the rows
+// longer than kLvxMaxDeg are left to k_level_index_long.
 __global__ void k_level_index(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
                               uint16_t* __restrict__ lvx) {
   for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n; v += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t rb = row_ptr[v], re = row_ptr[v + 1];
+    if (re - rb > kLvxMaxDeg) continue;
     for (uint32_t x = 1; x <= kLvxLevels; ++x)
-      lvx[size_t(x - 1) * size_t(n) + size_t(v)] = re - rb <= kLvxMaxDeg ? uint16_t(seg_lower(adj, rb, re, x) - rb) : 0;
+      lvx[size_t(x - 1) * size_t(n) + size_t(v)] = uint16_t(seg_lower(adj, rb, re, x) - rb);
   }
+}
+
+// Level index of the long rows: one thread per (long row h, level x); the
+// row's lvx entries hold h.
+__global__ void k_level_index_long(int32_t n, uint32_t n_long, const uint32_t* __restrict__ long_rows,
+                                   const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ adj,
+                                   uint16_t* __restrict__ lvx, uint32_t* __restrict__ lvx_long) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_long * kLvxLevels) return;
+  const uint32_t h = t / kLvxLevels, x = t % kLvxLevels + 1u, v = long_rows[h];
+  const uint32_t rb = row_ptr[v], re = row_ptr[v + 1];
+  lvx_long[t] = seg_lower(adj, rb, re, x) - rb;
+  lvx[size_t(x - 1) * size_t(n) + size_t(v)] = uint16_t(h);
 }
 
 int grid_for(int64_t work, int threads) {
@@ -393,6 +408,19 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
     cudaFree(d_cnt);
   }
   k_level_index<<<grid_for(n, T), T>>>(n, d_row, kg->d_adj, kg->d_lvx);
+  {
+    std::vector<uint32_t> long_rows;                   // fewer than 2^16: each holds > 2^16 of m2 < 2^32 entries
+    for (int64_t v = 0; v < n; ++v)
+      if (row32[v + 1] - row32[v] > kLvxMaxDeg) long_rows.push_back(uint32_t(v));
+    const uint32_t n_long = uint32_t(long_rows.size());
+    TRY(alloc_device((void**)&kg->d_lvx_long, sizeof(uint32_t) * kLvxLevels * size_t(n_long), &bytes));
+    if (n_long) {
+      // d_dl (m2 entries, no longer needed) holds the list of long rows
+      TRYC(cudaMemcpy(d_dl, long_rows.data(), sizeof(uint32_t) * n_long, cudaMemcpyHostToDevice));
+      const uint32_t tasks = n_long * kLvxLevels;
+      k_level_index_long<<<(tasks + T - 1) / T, T>>>(n, n_long, d_dl, d_row, kg->d_adj, kg->d_lvx, kg->d_lvx_long);
+    }
+  }
   TRYC(cudaGetLastError());
   TRYC(cudaDeviceSynchronize());
   cleanup();

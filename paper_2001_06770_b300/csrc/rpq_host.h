@@ -80,6 +80,7 @@ struct rpq_kg {
   uint32_t* d_adj = nullptr;
   uint8_t* d_amax = nullptr;
   uint16_t* d_lvx = nullptr;
+  uint32_t* d_lvx_long = nullptr;
   uint32_t* d_kw_ptr = nullptr;
   int32_t* d_kw_nodes = nullptr;
   int64_t device_bytes = 0;

@@ -46,9 +46,12 @@ enum DevErr : uint32_t {
   kErrTimeout = 1u << 8,   // a bounded grid barrier ran out
 };
 
-// Rows with at most kLvxMaxDeg entries carry a level index: lvx[x-1][v] is
-// the offset (from the row start) of the first entry with level >= x, for
-// x = 1..kLvxLevels.  Longer rows and higher levels use a binary search.
+// Level index of every row, for x = 1..kLvxLevels: for a row with at most
+// kLvxMaxDeg entries, lvx[x-1][v] is the offset (from the row start) of the
+// first entry with level >= x; a longer row (a hub; there are fewer than
+// 2^16 of them, as m2 < 2^32) stores its hub number h in every lvx[x-1][v],
+// and the offsets go to lvx_long[h * kLvxLevels + x-1] (32-bit).  Higher
+// levels use a binary search.
 constexpr uint32_t kLvxLevels = 8;
 constexpr uint32_t kLvxMaxDeg = 65535;
 
@@ -59,6 +62,7 @@ struct DevKG {
   const uint32_t* adj;
   const uint8_t* amax;
   const uint16_t* lvx;        // kLvxLevels * n, level-major
+  const uint32_t* lvx_long;   // kLvxLevels per row longer than kLvxMaxDeg
   int32_t n_kw;
   const uint32_t* kw_ptr;
   const int32_t* kw_nodes;
@@ -180,8 +184,9 @@ __device__ __forceinline__ uint32_t seg_lower(const uint32_t* adj, uint32_t lo, 
 // First entry of row v (bounds rb, re) whose level is >= x.
 __device__ __forceinline__ uint32_t seg_at(const DevKG& g, uint32_t v, uint32_t rb, uint32_t re, uint32_t x) {
   if (x == 0) return rb;
-  if (re - rb <= kLvxMaxDeg && x <= kLvxLevels) return rb + g.lvx[size_t(x - 1) * size_t(g.n) + v];
-  return seg_lower(g.adj, rb, re, x);
+  if (x > kLvxLevels) return seg_lower(g.adj, rb, re, x);
+  const uint32_t o = g.lvx[size_t(x - 1) * size_t(g.n) + v];
+  return rb + (re - rb <= kLvxMaxDeg ? o : g.lvx_long[size_t(o) * kLvxLevels + (x - 1)]);
 }
 
 __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {

@@ -279,6 +279,11 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   // completed reach w, the run stops at this level, so the level only needs
   // its identification: no work items, no retained frontier.
   const bool ident_only = run == 0 && ldx<P>(&c->ncg_at) + ldx<P>(&c->cg_next[p]) >= uint32_t(q.w);
+  // Marginal run: the V_C check of the previous level showed that the run
+  // stops at this level, and the RPG match above is all of its
+  // identification that can change the results (the PTC stops and work
+  // items of a level that is not expanded are never used): count Q_l only.
+  const bool count_only = run == 1 && l > 0 && ldx<P>(&c->skip_lvl) == l;
   if (blockIdx.x == 0 && threadIdx.x == 0) c->cg_next[p ^ 1] = 0;   // counted by k_expand of this level
   const uint32_t fq_n = ldx<P>(&c->fq_n[p]);
   const bool sparse = ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && fq_n <= s.fq_limit;
@@ -328,6 +333,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         const uint32_t pq = atomicAdd(&c->qlog_n, 1u);
         if (pq < s.qcap) s.qlog[pq] = (l << kNodeBits) | v; else atomicOr(&c->err, kErrOverflow);
       }
+      if (count_only) continue;                        // the same in every lane
       bool expand = false, is_cg = false, stop_now = false;
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
@@ -380,10 +386,12 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       }
       bool retain = false;
       if (expand) {
-        const bool indexed = re - rb <= kLvxMaxDeg;
-        const uint32_t hi = (indexed && l + 1 <= kLvxLevels) ? rb + o_hi : seg_lower(g.adj, rb, re, l + 1u);
-        const uint32_t lo = eq ? rb
-                               : (l == 0 ? rb : ((indexed && l <= kLvxLevels) ? rb + o_lo : seg_lower(g.adj, rb, hi, l)));
+        if (re - rb > kLvxMaxDeg) {                     // a hub: o_hi / o_lo hold its number
+          if (l + 1 <= kLvxLevels) o_hi = g.lvx_long[size_t(o_hi) * kLvxLevels + l];
+          if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx_long[size_t(o_lo) * kLvxLevels + (l - 1)];
+        }
+        const uint32_t hi = l + 1 <= kLvxLevels ? rb + o_hi : seg_lower(g.adj, rb, re, l + 1u);
+        const uint32_t lo = eq ? rb : (l == 0 ? rb : (l <= kLvxLevels ? rb + o_lo : seg_lower(g.adj, rb, hi, l)));
         retain = hi < re;                              // an edge with a > l remains
         if (hi > lo) {
           it_seg[r] = lo; it_len[r] = hi - lo; it_msk[r] = uint32_t(eq) | (uint32_t(lt) << 8);
@@ -391,7 +399,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
           my_work += hi - lo;
           // every eq column activates the prefix a <= l, every lt column the segment a == l
           uint32_t seg_l = lo;
-          if (eq && lt) seg_l = (indexed && l <= kLvxLevels) ? rb + o_lo : seg_lower(g.adj, rb, hi, l);
+          if (eq && lt) seg_l = l == 0 ? rb : (l <= kLvxLevels ? rb + o_lo : seg_lower(g.adj, rb, hi, l));
           eact += uint64_t(__popc(eq)) * (hi - rb) + uint64_t(__popc(lt)) * (hi - seg_l);
         }
       }

@@ -229,3 +229,36 @@ def test_alpha_sweep(alpha):
             trace_matches(kg.trace(q.central, q.marginal, q.k, q.max_depth, q.gamma), orc)
     finally:
         kg.close()
+
+
+def test_hub_rows_longer_than_the_16bit_level_index():
+    """Two hubs with 100k and 70k neighbours (rows beyond 2^16 entries, whose
+    level boundaries come from the 32-bit hub index) plus a sparse random
+    graph; 8 Zipf labels spread the hubs' edges over several activation
+    levels.  Keywords sit on hub neighbours and on random nodes."""
+    n = 150_000
+    rng = np.random.default_rng(7)
+    src = np.concatenate([np.zeros(99_999, np.uint32), np.ones(70_000, np.uint32),
+                          rng.integers(0, n, 300_000).astype(np.uint32)])
+    dst = np.concatenate([np.arange(1, 100_000, dtype=np.uint32), np.arange(2, 70_002, dtype=np.uint32),
+                          rng.integers(0, n, 300_000).astype(np.uint32)])
+    g = rpqgen.build_graph(n, src, dst, seed=7, n_labels=8, permute=False)
+    deg = np.diff(g.row_ptr)
+    assert deg[0] > 65535 and deg[1] > 65535
+    sets = [rng.choice(n, size=int(rng.integers(3, 40)), replace=False).tolist() for _ in range(8)]
+    sets[0] += [5, 70_500]
+    sets[1] += [99_000]
+    kp, kn = brute.postings_from_sets(8, sets)
+    abar = 3.0
+    act = oracle.activation(g.row_ptr, g.col, g.label, g.n_labels, 0.5, abar)
+    kg = rpq.KG(g.row_ptr, g.col, g.label, g.n_labels, kp, kn, 0.5, abar)
+    try:
+        adj, amax = kg.export()
+        assert np.array_equal(amax, act.amax)
+        for C, M, k in [([0, 1], [2, 3], 5), ([0, 1, 2], [4], 10), ([3], [5, 6], 3), ([4, 5], [6, 7, 0], 20)]:
+            orc = oracle.search(g, act.a, C, M, k, 8, kw_ptr=kp, kw_nodes=kn)
+            trace_matches(kg.trace(C, M, k, 8), orc)
+            res, _ = kg.search(C, M, k, 8)
+            results_match(res, orc)
+    finally:
+        kg.close()
