@@ -523,10 +523,11 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
       if (e < hi) {
         const uint32_t x = __ldg(g.adj + e);
         const uint32_t a = x >> kNodeBits, u = x & kNodeMask;
-        if ((vis_byte(s.vis, u) >> j) & 1u) {
-          const uint32_t hu = s.H[size_t(j) * s.hp + u];
+        const uint32_t vb = vis_byte(s.vis, u), hu = s.H[size_t(j) * s.hp + u];
+        const uint32_t cfw = s.cf[u >> 5], stl = s.stopl[u];
+        if ((vb >> j) & 1u) {
           const uint32_t lam = a > hu ? a : hu;
-          par = lam == l && !(((s.cf[u >> 5] >> (u & 31u)) & 1u) && s.stopl[u] <= l);
+          par = lam == l && !(((cfw >> (u & 31u)) & 1u) && stl <= l);
         }
       }
       found = __any_sync(0xffffffffu, par);
@@ -971,6 +972,18 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
 // holds a central keyword ORs its column mask into the union mask (vmask),
 // every column mask is cleared, and the last CTA of all columns turns the
 // union masks into V_C of each CG.
+// Node v holds a central keyword (h = 0 in a column it was reached in).
+__device__ __forceinline__ bool holds_central(const DevSlot& s, const QueryDev& q, uint32_t v) {
+  const uint32_t vb = vis_byte(s.vis, v);
+  uint32_t h[kMaxCols];
+#pragma unroll
+  for (int jj = 0; jj < kMaxCols; ++jj) h[jj] = jj < q.n_c ? s.H[size_t(jj) * s.hp + v] : 1u;
+  bool holds = false;
+#pragma unroll
+  for (int jj = 0; jj < kMaxCols; ++jj) holds |= ((vb >> jj) & 1u) && h[jj] == 0;
+  return holds;
+}
+
 __global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads, 1)
 k_recover_cols(DevKG g, DevSlot s) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -1019,10 +1032,19 @@ k_recover_cols(DevKG g, DevSlot s) {
       unsigned long long m = 0;
       if (i < cnt) {
         const uint32_t qn = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
-        if (i < nseg || Hj[qn] == uint8_t(x)) {
-          rb = g.row_ptr[qn];
-          len = seg_at(g, qn, rb, g.row_ptr[qn + 1], uint32_t(x)) - rb;   // edges with a <= x-1
-          m = __ldcg(rmask + qn);
+        // every load of the node first (the addresses depend on qn alone)
+        const uint32_t hq = Hj[qn];
+        const uint32_t r0 = g.row_ptr[qn], r1 = g.row_ptr[qn + 1];
+        const uint32_t o = uint32_t(x) <= kLvxLevels ? g.lvx[size_t(x - 1) * size_t(g.n) + qn] : 0u;
+        const unsigned long long mq = __ldcg(rmask + qn);
+        if (i < nseg || hq == uint32_t(x)) {
+          uint32_t hi;                               // first entry with a >= x
+          if (uint32_t(x) > kLvxLevels) hi = seg_lower(g.adj, r0, r1, uint32_t(x));
+          else if (r1 - r0 <= kLvxMaxDeg) hi = r0 + o;
+          else hi = r0 + g.lvx_long[size_t(o) * kLvxLevels + (x - 1)];
+          rb = r0;
+          len = hi - r0;                             // edges with a <= x-1
+          m = mq;
         }
       }
       uint64_t tot = 0;
@@ -1039,11 +1061,12 @@ k_recover_cols(DevKG g, DevSlot s) {
         }
         const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
         const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
-        if (!((vis_byte(s.vis, nb) >> j) & 1u)) continue;
-        const uint32_t hn = Hj[nb];
+        // all loads of the neighbour at once, then the tests
+        const uint32_t vb = vis_byte(s.vis, nb), hn = Hj[nb], cfw = s.cf[nb >> 5], stl = s.stopl[nb];
+        if (!((vb >> j) & 1u)) continue;
         const uint32_t lam = a > hn ? a : hn;
         if (lam + 1 != uint32_t(x)) continue;                               // not tight
-        if (((s.cf[nb >> 5] >> (nb & 31u)) & 1u) && s.stopl[nb] <= lam) continue;  // nb had stopped
+        if (((cfw >> (nb & 31u)) & 1u) && stl <= lam) continue;             // nb had stopped
         if (atomicOr(&rmask[nb], s_m[lo]) != 0) continue;                  // already listed
         if (hn + 1 == uint32_t(x)) {
           const uint32_t p = next_base + atomicAdd(&sn[hn], 1u);
@@ -1064,10 +1087,7 @@ k_recover_cols(DevKG g, DevSlot s) {
     const uint32_t v = i < nseg ? __ldcg(rlist + i) : __ldcg(rlist + cap - 1u - (i - nseg));
     const unsigned long long m = __ldcg(rmask + v);
     rmask[v] = 0;
-    const uint32_t vb = vis_byte(s.vis, v);
-    bool holds = false;
-    for (int jj = 0; jj < q.n_c; ++jj) holds |= ((vb >> jj) & 1u) && s.H[size_t(jj) * s.hp + v] == 0;
-    if (!holds) continue;
+    if (!holds_central(s, q, v)) continue;
     const unsigned long long old = atomicOr(&s.vmask[v], m);
     if (old == 0) {
       const uint32_t p = atomicAdd(&c->ulist_n, 1u);
@@ -1092,10 +1112,7 @@ k_recover_cols(DevKG g, DevSlot s) {
     const uint32_t v = __ldcg(s.ulist + i);
     unsigned long long m = __ldcg(s.vmask + v);
     s.vmask[v] = 0;
-    const uint32_t vb = vis_byte(s.vis, v);
-    bool holds = false;
-    for (int jj = 0; jj < q.n_c; ++jj) holds |= ((vb >> jj) & 1u) && s.H[size_t(jj) * s.hp + v] == 0;
-    if (!holds) continue;
+    if (!holds_central(s, q, v)) continue;
     for (; m; m &= m - 1) {
       const uint32_t gi = __ffsll(m) - 1;
       const uint32_t p = atomicAdd(&c->nvc, 1u);
