@@ -232,7 +232,7 @@ __device__ bool theorem4_stop(const Ctl* c, const uint8_t* matched, const uint8_
 // keywords is a CG with S^c = max_j h (Theorem 3) and stops expanding;
 // marginal run with |M| >= 2, a node reached by all marginal keywords stops
 // (PTC).  Nodes still expanding become work items with their newly active
-// segment; retained nodes (an edge with a > l) go to F_{l+1}.  Block 0 of
+// segment; retained nodes (an edge with a > l) go to F_{l+1}.  The last block of
 // the marginal run also performs the RPG identification of the level.
 // Items are compacted with warp ballots, a block scan and one 64-bit
 // atomicAdd per block tile; each item also marks the warp tiles of the
@@ -252,9 +252,10 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_acc[kMaxK];
 
-  if (run == 1 && blockIdx.x == 0) {
+  if (run == 1 && blockIdx.x == gridDim.x - 1u) {
     // RPG identification: a selected CG matches when every marginal keyword
     // has reached some node of its V_C; then S^m = max_i min_{v in V_C} h = l.
+    // (The last block: on a short level the first blocks hold the frontier.)
     const uint32_t nsel = ldx<P>(&c->nsel);
     for (uint32_t i = threadIdx.x; i < kMaxK; i += blockDim.x) s_acc[i] = 0;
     __syncthreads();
@@ -817,26 +818,60 @@ k_run(DevKG g, DevSlot s, int run) {
 // One launch.  Keys are (S^c << 26) | node, so ascending order is the
 // (S^c, node id) order of the selection.  Each block takes chunks of up to
 // kTopkChunk CG keys and keeps the w smallest it has seen (the w-th smallest
-// of a chunk is found by a three-round radix select over 12/10/10-bit digits
-// with shared-memory histograms; only keys up to it are kept); the last block
+// of a chunk is found by a radix select over the key offsets from the chunk's
+// smallest key, up to 11 bits per round: two rounds when the keys share S^c
+// and the node ids span up to 2^22; only keys up to it are kept); the last block
 // to finish selects the w smallest of all blocks' survivors the same way,
 // orders them by rank and writes the selected CGs.
 
-// The K-th smallest (1-based, K <= number of valid keys) of keys[0..len);
-// 0xffffffff marks an empty entry.  All threads of the block call it.
-__device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
-                                  uint64_t* s_warp, uint32_t* s_bin) {
-  uint32_t prefix = 0, pmask = 0, need = K;
+// Smallest and largest valid key of keys[0..len) and their count (0xffffffff
+// marks an empty entry); all threads of the block call it and get the result.
+__device__ void block_key_range(const uint32_t* keys, uint32_t len, uint32_t* s_red, uint32_t& kmin,
+                                uint32_t& kmax, uint32_t& cnt) {
+  uint32_t mn = 0xffffffffu, mx = 0, n = 0;
+  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+    const uint32_t k = keys[i];
+    if (k == 0xffffffffu) continue;
+    mn = min(mn, k); mx = max(mx, k); ++n;
+  }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  n = __reduce_add_sync(0xffffffffu, n);
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) { s_red[warp] = mn; s_red[32 + warp] = mx; s_red[64 + warp] = n; }
+  __syncthreads();
+  if (warp == 0) {
+    const bool in = lane < nw;
+    mn = __reduce_min_sync(0xffffffffu, in ? s_red[lane] : 0xffffffffu);
+    mx = __reduce_max_sync(0xffffffffu, in ? s_red[32 + lane] : 0u);
+    n = __reduce_add_sync(0xffffffffu, in ? s_red[64 + lane] : 0u);
+    if (lane == 0) { s_red[96] = mn; s_red[97] = mx; s_red[98] = n; }
+  }
+  __syncthreads();
+  kmin = s_red[96]; kmax = s_red[97]; cnt = s_red[98];
+  __syncthreads();
+}
+
+// The K-th smallest (1-based, K <= number of valid keys) of keys[0..len),
+// all of whose valid keys lie in [lo, lo + 2^span): a radix select over the
+// offsets from lo, most significant digits first, up to 11 bits per round
+// with a shared-memory histogram.  All threads of the block call it.
+__device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K, uint32_t lo, uint32_t span,
+                                  uint32_t* hist, uint64_t* s_warp, uint32_t* s_bin) {
+  uint64_t prefix = 0;                                   // decided high bits of the offset
+  uint32_t need = K;
   const uint32_t nt = blockDim.x;
 #pragma unroll 1
-  for (int r = 0; r < 3; ++r) {
-    const uint32_t bits = r == 0 ? 12u : 10u, sh = r == 0 ? 20u : (r == 1 ? 10u : 0u);
+  for (uint32_t rem = span; rem > 0;) {
+    const uint32_t bits = min(rem, 11u), sh = rem - bits;
     const uint32_t B = 1u << bits, per = (B + nt - 1) / nt;
     for (uint32_t i = threadIdx.x; i < B; i += nt) hist[i] = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < len; i += nt) {
       const uint32_t k = keys[i];
-      if (k != 0xffffffffu && (k & pmask) == prefix) atomicAdd(&hist[(k >> sh) & (B - 1u)], 1u);
+      if (k == 0xffffffffu) continue;
+      const uint64_t d = uint64_t(k - lo);
+      if ((d >> rem) == (prefix >> rem)) atomicAdd(&hist[uint32_t(d >> sh) & (B - 1u)], 1u);
     }
     __syncthreads();
     uint32_t local = 0;
@@ -849,23 +884,21 @@ __device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K
     }
     __syncthreads();
     need -= s_bin[1];
-    prefix |= s_bin[0] << sh;
-    pmask |= (B - 1u) << sh;
+    prefix |= uint64_t(s_bin[0]) << sh;
+    rem = sh;
     __syncthreads();
   }
-  return prefix;
+  return lo + uint32_t(prefix);
 }
 
 // Keep the (at most) K smallest valid keys of keys[0..len) in place; returns their count.
 __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
-                                        uint64_t* s_warp, uint32_t* s_bin) {
-  for (uint32_t i = threadIdx.x; i < 2; i += blockDim.x) s_bin[2 + i] = 0;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
-    if (keys[i] != 0xffffffffu) atomicAdd(&s_bin[2], 1u);
-  __syncthreads();
-  const uint32_t valid = s_bin[2];
-  const uint32_t t = valid > K ? block_kth_key(keys, len, K, hist, s_warp, s_bin) : 0xfffffffeu;
+                                        uint64_t* s_warp, uint32_t* s_bin, uint32_t* s_red) {
+  if (threadIdx.x == 0) s_bin[3] = 0;
+  uint32_t kmin, kmax, valid;
+  block_key_range(keys, len, s_red, kmin, kmax, valid);   // ends with a barrier
+  const uint32_t span = kmax > kmin ? 32u - uint32_t(__clz(kmax - kmin)) : 0u;
+  const uint32_t t = valid > K ? block_kth_key(keys, len, K, kmin, span, hist, s_warp, s_bin) : 0xfffffffeu;
   // compact keys <= t to the front (order is restored by the final ranking)
   uint32_t mine[kTopkChunk / kTopkThreads];
   uint32_t nm = 0;
@@ -883,9 +916,10 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
   const uint32_t n_in = min(c->ncg, s.cap);
   const uint32_t nchunks = (n_in + kTopkChunk - 1) / kTopkChunk;
   __shared__ uint32_t key[kTopkChunk + 2 * kMaxK];
-  __shared__ uint32_t hist[4096];
+  __shared__ uint32_t hist[2048];
   __shared__ uint64_t s_warp[33];
   __shared__ uint32_t s_bin[4];
+  __shared__ uint32_t s_red[100];
   __shared__ uint32_t s_keep, s_last;
   uint32_t* keep = key + kTopkChunk;                     // survivors of this block (<= 2K while merging)
   if (threadIdx.x == 0) s_keep = 0;
@@ -895,12 +929,12 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     const uint32_t len = min(uint32_t(kTopkChunk), n_in - b);
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) key[i] = s.cg[b + i];
     __syncthreads();
-    const uint32_t m = block_keep_smallest(key, len, K, hist, s_warp, s_bin);
+    const uint32_t m = block_keep_smallest(key, len, K, hist, s_warp, s_bin, s_red);
     // merge with the survivors of earlier chunks
     const uint32_t k0 = s_keep;
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) keep[k0 + i] = key[i];
     __syncthreads();
-    const uint32_t mm = block_keep_smallest(keep, k0 + m, K, hist, s_warp, s_bin);
+    const uint32_t mm = block_keep_smallest(keep, k0 + m, K, hist, s_warp, s_bin, s_red);
     if (threadIdx.x == 0) s_keep = mm;
     __syncthreads();
   }
@@ -922,7 +956,7 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     total += K;
     if (total + K > uint32_t(kTopkChunk) || blk + 1 == nb) {
       __syncthreads();
-      total = block_keep_smallest(key, total, K, hist, s_warp, s_bin);
+      total = block_keep_smallest(key, total, K, hist, s_warp, s_bin, s_red);
       __syncthreads();
     }
   }
