@@ -163,7 +163,8 @@ def _check(rc: int):
 
 
 def _ptr(a):
-    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    # the address as a Python int: every argument and field it feeds is c_void_p
+    return None if a is None else a.ctypes.data
 
 
 def topk_keys_noalloc(d_keys: int, n: int, k: int, d_out: int, d_n_out: int, stream: int = 0):

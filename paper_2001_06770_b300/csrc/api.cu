@@ -68,8 +68,7 @@ void destroy_slot(Slot* s) {
   if (s->st) cudaStreamSynchronize(s->st);
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (void* p : s->allocs) cudaFree(p);
-  if (s->h_ctl) cudaFreeHost(s->h_ctl);
-  if (s->h_res) cudaFreeHost(s->h_res);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);            // h_res lies inside it
   if (s->st) cudaStreamDestroy(s->st);
   delete s;
 }
@@ -136,9 +135,9 @@ int create_slot(rpq_kg* kg, Slot** out) {
   d.tgt_cap = d.cap;
   SA(d.tgt, sizeof(uint32_t) * d.tgt_cap);
   SA(d.sticky, 16);
-  SA(d.ctl, sizeof(Ctl));
+  SA(d.ctl, kCtlBytes + sizeof(rpq_result) * kMaxK);   // the results follow the control block:
+  if (rc == RPQ_OK) d.res = reinterpret_cast<char*>(d.ctl) + kCtlBytes;   // one copy returns both
   SA(d.q, sizeof(QueryDev));
-  SA(d.res, sizeof(rpq_result) * kMaxK);
   SA(d.n_res, 16);
   SA(d.bar, 16);
 #undef SA
@@ -150,14 +149,14 @@ int create_slot(rpq_kg* kg, Slot** out) {
         cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
         cudaMemset(d.bar, 0, 16) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl)) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_res, sizeof(rpq_result) * kMaxK) != cudaSuccess) {
+        cudaMallocHost((void**)&s->h_ctl, kCtlBytes + sizeof(rpq_result) * kMaxK) != cudaSuccess) {
       cudaGetLastError();
       set_error(RPQ_ENOMEM, "search slot set-up failed");
       rc = RPQ_ENOMEM;
     }
   }
   if (rc != RPQ_OK) { destroy_slot(s); return rc; }
+  s->h_res = reinterpret_cast<rpq_result*>(reinterpret_cast<char*>(s->h_ctl) + kCtlBytes);
   d.qlog = nullptr;
   d.qcap = 0;
   d.target = use_target() ? 1u : 0u;
@@ -353,8 +352,8 @@ int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
   if (rc != RPQ_OK) { set_error(RPQ_ECUDA, "launch failed: %s", cudaGetErrorString(cudaGetLastError())); return rc; }
   rc = enqueue_body(kg, s, qv.n_c, qv.n_m, qv.L);
   if (rc != RPQ_OK) return rc;
-  RPQ_CUDA(cudaMemcpyAsync(s->h_ctl, s->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->st));
-  RPQ_CUDA(cudaMemcpyAsync(s->h_res, s->d.res, sizeof(rpq_result) * size_t(qv.k), cudaMemcpyDeviceToHost, s->st));
+  RPQ_CUDA(cudaMemcpyAsync(s->h_ctl, s->d.ctl, kCtlBytes + sizeof(rpq_result) * size_t(qv.k),
+                           cudaMemcpyDeviceToHost, s->st));      // control block and results
   s->busy = true;
   s->pending_k = qv.k;
   s->pending_nm = qv.n_m;

@@ -32,7 +32,7 @@ struct Slot {
   cudaStream_t st = nullptr;
   int64_t bytes = 0;
   Ctl* h_ctl = nullptr;
-  rpq_result* h_res = nullptr;
+  rpq_result* h_res = nullptr;   // inside the h_ctl allocation, kCtlBytes after its start
   std::vector<void*> allocs;
   std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
   bool busy = false;

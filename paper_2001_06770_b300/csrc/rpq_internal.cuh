@@ -125,6 +125,10 @@ struct Ctl {
   uint8_t sm[kMaxK];
 };
 
+// Bytes of the control block in a slot's control allocation; the results
+// (rpq_result[kMaxK]) follow it there, so one copy returns both.
+constexpr size_t kCtlBytes = (sizeof(Ctl) + 15) / 16 * 16;
+
 struct DevSlot {
   uint8_t* H;
   uint32_t* vis;
