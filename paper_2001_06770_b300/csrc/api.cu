@@ -293,7 +293,6 @@ static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, int L, int K, cudaGra
       launch_run_setup(kg->dev, s->d, 1, s->st, nullptr);
       add_run(1);
     }
-    launch_results(s->d, s->st, nullptr);
   }
   if (capturing) {
     cudaGraph_t got = nullptr;

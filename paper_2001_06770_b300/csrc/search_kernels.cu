@@ -15,7 +15,9 @@
 //                                     (Algorithm 1) of the newly active edges
 //   after the central run: k_topk (top-w CGs),
 //                          k_recover_cols (Algorithm 2 -> V_C)
-//   at the end:            k_results (Eq. 6, top-k by (S^r, id))
+//   the results (Eq. 6, top-k by (S^r, id)) are written by the kernel that
+//   ends the search: k_topk when there is no marginal run, else the k_expand
+//   that stops the marginal run (no launch of their own)
 // The Glevel is kept in the control block, so the level kernels form the body
 // of a CUDA-graph WHILE node that k_expand ends when the run stops, or the
 // L+1 early-exit repetitions of a flat graph; the graph of each query shape
@@ -138,6 +140,9 @@ __device__ __forceinline__ void queue_push(const DevSlot& s, Ctl* c, int p, bool
   base = __shfl_sync(0xffffffffu, base, 0);
   if (flag && base != 0xffffffffu) s.fq[p][base + __popc(b & ((1u << lane) - 1u))] = v;
 }
+
+// Eq. 6 scores and the top-k results of the query (defined below).
+__device__ void write_results(const DevSlot& s);
 
 // Initialisation (Section 4.2.1): keyword nodes get h = 0 and become frontiers.
 __global__ void k_seed(DevKG g, DevSlot s, int run) {
@@ -662,6 +667,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       c->fq_over[p] = 0;
     }
   }
+  if (stop && run == 1 && blockIdx.x == 0) write_results(s);   // the marginal run ends here
   if (stop || skip || n_work == 0) return stop;
 
   __shared__ uint64_t s_warp[33];
@@ -978,7 +984,10 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     c->ulist_n = 0;
     c->nvc = 0;
     c->topk_done = 0;
+    __threadfence();
   }
+  __syncthreads();
+  if (s.q->n_m == 0 || total == 0) write_results(s);   // no marginal run follows
 }
 
 // ---------------------------------------------------------------- recovery
@@ -1159,37 +1168,45 @@ k_recover_cols(DevKG g, DevSlot s) {
 // --------------------------------------------------------------- results
 // Eq. 6 (or product) scores and the top-k by (S^r, node id).  With M empty
 // the results are the selected CGs with S^m = 0 and S^r = S^c.
-__global__ void k_results(DevSlot s) {
+// Needs at least kMaxK threads of one block; every thread of the block calls it.
+// The control block is read through L2: inside one persistent launch other
+// blocks wrote it.
+__device__ void write_results(const DevSlot& s) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   rpq_result* out = reinterpret_cast<rpq_result*>(s.res);
-  const uint32_t nsel = c->nsel;
+  const uint32_t nsel = __ldcg(&c->nsel);
   __shared__ double s_sr[kMaxK];
   __shared__ uint32_t s_ok[kMaxK];
+  __shared__ int32_t s_node[kMaxK];
+  __shared__ uint32_t s_sc[kMaxK], s_sm[kMaxK];
   const uint32_t gi = threadIdx.x;
   if (gi < kMaxK) {
     s_ok[gi] = 0;
     if (gi < nsel) {
-      if (q.n_m == 0) { s_ok[gi] = 1; s_sr[gi] = double(c->sel_sc[gi]); }
-      else if (c->matched[gi]) {
+      s_node[gi] = __ldcg(&c->sel[gi]);
+      s_sc[gi] = __ldcg(&c->sel_sc[gi]);
+      s_sm[gi] = q.n_m == 0 ? 0u : uint32_t(__ldcg(&c->sm[gi]));
+      if (q.n_m == 0) { s_ok[gi] = 1; s_sr[gi] = double(s_sc[gi]); }
+      else if (__ldcg(&c->matched[gi])) {
         s_ok[gi] = 1;
-        s_sr[gi] = rpg_score(q, c->sel_sc[gi], c->sm[gi]);
+        s_sr[gi] = rpg_score(q, s_sc[gi], s_sm[gi]);
       }
     }
   }
   __syncthreads();
   if (gi < nsel && s_ok[gi]) {
-    const int32_t node = c->sel[gi];
+    const int32_t node = s_node[gi];
     uint32_t rank = 0;
     for (uint32_t o = 0; o < nsel; ++o) {
       if (!s_ok[o] || o == gi) continue;
-      if (s_sr[o] < s_sr[gi] || (s_sr[o] == s_sr[gi] && c->sel[o] < node)) ++rank;
+      if (s_sr[o] < s_sr[gi] || (s_sr[o] == s_sr[gi] && s_node[o] < node)) ++rank;
     }
     if (rank < uint32_t(q.k)) {
       rpq_result r;
       r.node = node;
-      r.s_c = c->sel_sc[gi];
-      r.s_m = q.n_m == 0 ? 0 : c->sm[gi];
+      r.s_c = int32_t(s_sc[gi]);
+      r.s_m = int32_t(s_sm[gi]);
       r.reserved = 0;
       r.s_r = s_sr[gi];
       out[rank] = r;
@@ -1202,9 +1219,15 @@ __global__ void k_results(DevSlot s) {
     n = min(n, uint32_t(q.k));
     c->n_res = n;
     *s.n_res = int32_t(n);
-    if (c->err) atomicOr(s.sticky, c->err);
+    const uint32_t err = __ldcg(&c->err);
+    if (err) atomicOr(s.sticky, err);
   }
 }
+
+// Standalone form (trace and subgraph paths); a query graph has no such node:
+// the kernel that ends the search writes the results itself (k_topk when
+// there is no marginal run, else the k_expand that stops the marginal run).
+__global__ void k_results(DevSlot s) { write_results(s); }
 
 }  // namespace
 
@@ -1318,7 +1341,6 @@ int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStre
     if (s.persistent) launch_run_persistent(g, s, 1, st, prof);
     else levels(1);
   }
-  launch_results(s, st, prof);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
@@ -1347,8 +1369,8 @@ int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaS
 // Kernels launched by one query in a graph (for launch accounting): fixed
 // kernels plus, per run, two per executed Glevel or one persistent launch.
 int kernels_fixed_per_query(int n_m) {
-  // k_set_query, k_seed, k_topk, [k_recover_cols, k_run_start, k_seed], k_results
-  return 1 + 1 + 1 + (n_m > 0 ? 3 : 0) + 1;
+  // k_set_query, k_seed, k_topk, [k_recover_cols, k_run_start, k_seed]
+  return 1 + 1 + 1 + (n_m > 0 ? 3 : 0);
 }
 
 }  // namespace rpq

@@ -46,7 +46,7 @@ def test_autotune(small):
     ds, kg, qs, orc = small
     t = kg.autotune(qs[:6], repeats=1)
     assert t["queue_div"] in (8, 32, 128) and t["next_queue_mult"] in (4, 16, 64)
-    assert t["batch_slots"] in (4, 8, 16)
+    assert t["batch_slots"] in (4, 8, 16, 32) and t["flat_levels"] in (2, 3, 4, 6, 64)
     assert kg.tuning() == t
     for q, o in zip(qs, orc):
         results_match(kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)[0], o)
