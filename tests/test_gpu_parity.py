@@ -56,8 +56,12 @@ def test_search_matches_trace_and_oracle(bundle):
         results_match(res, orc)
         if orc.central is not None:
             assert st["e_act_central"] == orc.central.e_act
+            assert st["levels_central"] == orc.central.last_level
         if orc.marginal is not None:
+            # E_act and the stop level stay exact when the V_C check skips the
+            # last expansion and the last enqueue only counts the frontier
             assert st["e_act_marginal"] == orc.marginal.e_act
+            assert st["levels_marginal"] == orc.marginal.last_level
 
 
 def test_batch_equals_one_at_a_time(bundle):
