@@ -259,10 +259,12 @@ def test_hub_rows_longer_than_the_16bit_level_index():
     try:
         adj, amax = kg.export()
         assert np.array_equal(amax, act.amax)
-        for C, M, k in [([0, 1], [2, 3], 5), ([0, 1, 2], [4], 10), ([3], [5, 6], 3), ([4, 5], [6, 7, 0], 20)]:
-            orc = oracle.search(g, act.a, C, M, k, 8, kw_ptr=kp, kw_nodes=kn)
-            trace_matches(kg.trace(C, M, k, 8), orc)
-            res, _ = kg.search(C, M, k, 8)
+        # depth 12 also takes the binary search above the indexed levels 1..8
+        for C, M, k, L in [([0, 1], [2, 3], 5, 8), ([0, 1, 2], [4], 10, 8), ([3], [5, 6], 3, 8),
+                           ([4, 5], [6, 7, 0], 20, 8), ([0, 6], [1, 7], 20, 12), ([2, 3, 4], [5], 40, 12)]:
+            orc = oracle.search(g, act.a, C, M, k, L, kw_ptr=kp, kw_nodes=kn)
+            trace_matches(kg.trace(C, M, k, L), orc)
+            res, _ = kg.search(C, M, k, L)
             results_match(res, orc)
     finally:
         kg.close()
