@@ -321,7 +321,7 @@ def run(args):
         qs = qs[:args.queries]
     kg = rpq.KG.from_dataset(ds)
     # work-split parameters picked by the library's autotuner on a sample
-    tuned = kg.autotune(qs[:16], repeats=2) if args.autotune else kg.tuning()
+    tuned = kg.autotune(qs[:args.tune_queries], repeats=2) if args.autotune else kg.tuning()
     args.tuning = tuned
     if wl["mode"] == "batch":
         line = run_batch(args, ws, rank, local, wl, ds, qs, kg)
@@ -573,6 +573,7 @@ def main():
                     help="medium (default, the benchmark line), large, batched or served")
     ap.add_argument("--queries", type=int, default=0, help="use only the first Q queries of the workload")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's autotuner first (1) or not (0)")
+    ap.add_argument("--tune-queries", type=int, default=16, help="queries of the workload the autotuner times")
     ap.add_argument("--profile-only", type=int, default=0, metavar="Q",
                     help="load the workload, run its first Q queries once through rpq_search and exit "
                          "(a short command for ncu captures); prints no JSON line")
