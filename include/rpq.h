@@ -344,8 +344,8 @@ int rpq_slot_stream(rpq_kg *kg, int32_t slot, void **stream);
  * returns the accumulated device milliseconds and launch counts per kernel
  * class and, with reset != 0, clears them.  A search writes its results from
  * the kernel that ends it (the top-w selection, or the expansion that stops
- * the marginal run), so RPQ_PROF_RESULTS stays at zero for rpq_search; only
- * the trace path launches a results kernel of its own. */
+ * the marginal run), so RPQ_PROF_RESULTS stays at zero (the trace and
+ * subgraph calls launch a results kernel of their own, untimed). */
 enum { RPQ_PROF_SETUP = 0, RPQ_PROF_ENQUEUE, RPQ_PROF_EXPAND, RPQ_PROF_TOPK, RPQ_PROF_RECOVER,
        RPQ_PROF_RESULTS, RPQ_PROF_CLASSES };
 typedef struct {
