@@ -60,6 +60,11 @@ def _L():
         _lib.orc_get_h.argtypes = [P, i32, P, P, i32]
         _lib.orc_get_h.restype = i32
         _lib.orc_free.argtypes = [P]
+        _lib.orc_graph_new.argtypes = [i32, i64, P, P, P, i32, P, P]
+        _lib.orc_graph_new.restype = P
+        _lib.orc_graph_free.argtypes = [P]
+        _lib.orc_search_graph.argtypes = [P, P, i32, P, i32, i32, i32, f64, i32, i32, i32, i32, u64, i32]
+        _lib.orc_search_graph.restype = P
     return _lib
 
 
@@ -97,9 +102,59 @@ def activation(row_ptr, col, label, n_labels, alpha, abar) -> Activation:
     return Activation(a, amax, cnt, w, x)
 
 
-def dataset_activation(ds) -> Activation:
+def dataset_activation(ds, detail: bool = True) -> Activation:
+    """Activation levels of a dataset's graph.  With ``detail=False`` only
+    ``a`` and ``amax`` are kept (the per-entry counts, weights and values before
+    rounding take 24 bytes per CSR entry; they are None then)."""
     g = ds.graph
-    return activation(g.row_ptr, g.col, g.label, g.n_labels, ds.alpha, ds.abar)
+    if detail:
+        return activation(g.row_ptr, g.col, g.label, g.n_labels, ds.alpha, ds.abar)
+    row_ptr = np.ascontiguousarray(g.row_ptr, np.int64)
+    col = np.ascontiguousarray(g.col, np.int32)
+    label = np.ascontiguousarray(g.label, np.uint16)
+    n = len(row_ptr) - 1
+    a = np.empty(int(row_ptr[-1]), np.uint8)
+    amax = np.empty(n, np.uint8)
+    rc = _L().orc_activation(n, int(row_ptr[-1]), _p(row_ptr), _p(col), _p(label), int(g.n_labels),
+                             float(ds.alpha), float(ds.abar), _p(a), _p(amax), None, None, None)
+    if rc != 0:
+        raise ValueError("orc_activation rejected its arguments")
+    return Activation(a, amax, None, None, None)
+
+
+class PreparedGraph:
+    """A graph with its CSR transpose built once (``orc_graph_new``), for many
+    searches.  The C side only reads it, so searches may run on it from several
+    threads at once (the ctypes calls release the GIL).  Holds references to
+    the arrays it was built from."""
+
+    def __init__(self, ds_or_graph, a: np.ndarray, kw_ptr=None, kw_nodes=None):
+        if hasattr(ds_or_graph, "graph"):
+            g = ds_or_graph.graph
+            kw_ptr, kw_nodes = ds_or_graph.kw_ptr, ds_or_graph.kw_nodes
+        else:
+            g = ds_or_graph
+        self.row_ptr = np.ascontiguousarray(g.row_ptr, np.int64)
+        self.col = np.ascontiguousarray(g.col, np.int32)
+        self.a = np.ascontiguousarray(a, np.uint8)
+        self.kw_ptr = np.ascontiguousarray(kw_ptr, np.int64)
+        self.kw_nodes = np.ascontiguousarray(kw_nodes, np.int32)
+        self.n = len(self.row_ptr) - 1
+        self.handle = _L().orc_graph_new(self.n, int(self.row_ptr[-1]), _p(self.row_ptr), _p(self.col), _p(self.a),
+                                         len(self.kw_ptr) - 1, _p(self.kw_ptr), _p(self.kw_nodes))
+        if not self.handle:
+            raise ValueError("orc_graph_new rejected its arguments")
+
+    def close(self):
+        if self.handle:
+            _L().orc_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass
@@ -152,9 +207,13 @@ def _scalar(L, h, field, r=0, dtype=np.int32):
     return int(out[0])
 
 
-def _run(L, h, r, n) -> RunTrace | None:
+def _run(L, h, r, n, trace=True) -> RunTrace | None:
     if not _scalar(L, h, F_RAN, r):
         return None
+    if not trace:       # counts only: no hit-level table, stop levels or frontiers
+        return RunTrace(h=None, stop=None, frontiers=None, last_level=_scalar(L, h, F_LAST_LEVEL, r),
+                        last_expanded=_scalar(L, h, F_LAST_EXPANDED, r),
+                        e_act=_scalar(L, h, F_EACT, r, np.int64), new_hits=_scalar(L, h, F_NEWHITS, r, np.int64))
     nt = L.orc_get_h(h, r, None, None, n)
     H = np.empty((n, max(nt, 1)), np.uint8)
     stop = np.empty(n, np.uint8)
@@ -169,10 +228,20 @@ def _run(L, h, r, n) -> RunTrace | None:
 
 def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int, gamma: float = 0.5,
            disable_stops: bool = False, exhaustive_marginal: bool = False, shuffle_seed: int = 0,
-           kw_ptr=None, kw_nodes=None, w: int = 0, product: bool = False) -> SearchResult:
+           kw_ptr=None, kw_nodes=None, w: int = 0, product: bool = False, prepared: PreparedGraph = None,
+           trace: bool = True, subgraphs: bool = True) -> SearchResult:
     """Run the oracle on one query.  ``ds_or_graph`` is an ``rpqgen.Dataset`` or
     an ``rpqgen.Graph`` (then pass ``kw_ptr``/``kw_nodes``).  ``w`` is the CG
-    beam width (0: w = k), ``product`` selects the multiplicative S^r."""
+    beam width (0: w = k), ``product`` selects the multiplicative S^r.
+
+    With ``prepared`` (a PreparedGraph of the same graph and levels) the
+    graph arguments are ignored and the transpose is not rebuilt.
+    ``trace=False`` keeps no frontiers, hit-level tables or stop levels (the
+    runs' counts and levels remain); ``subgraphs=False`` builds no G^m and
+    checks no PTC (vm, em and ptc are None).  Neither changes a result."""
+    if prepared is not None:
+        return _search_prepared(prepared, central, marginal, k, max_depth, gamma, disable_stops,
+                                exhaustive_marginal, shuffle_seed, w, product, trace, subgraphs)
     if hasattr(ds_or_graph, "graph"):
         g = ds_or_graph.graph
         kw_ptr, kw_nodes = ds_or_graph.kw_ptr, ds_or_graph.kw_nodes
@@ -191,13 +260,29 @@ def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int
                      _p(kw_nodes), _p(c), len(c), _p(m) if len(m) else None, len(m), int(k),
                      int(max_depth), float(gamma), int(w), int(bool(product)), int(disable_stops),
                      int(exhaustive_marginal), int(shuffle_seed))
+    return _collect(L, h, n, True, True)
+
+
+def _search_prepared(pg, central, marginal, k, max_depth, gamma, disable_stops, exhaustive_marginal,
+                     shuffle_seed, w, product, trace, subgraphs) -> SearchResult:
+    L = _L()
+    c = np.ascontiguousarray(central, np.int32)
+    m = np.ascontiguousarray(marginal, np.int32)
+    flags = (1 if trace else 0) | (2 if subgraphs else 0)
+    h = L.orc_search_graph(pg.handle, _p(c), len(c), _p(m) if len(m) else None, len(m), int(k), int(max_depth),
+                           float(gamma), int(w), int(bool(product)), int(disable_stops),
+                           int(exhaustive_marginal), int(shuffle_seed), flags)
+    return _collect(L, h, pg.n, trace, subgraphs)
+
+
+def _collect(L, h, n, trace, subgraphs) -> SearchResult:
     try:
         nsel = _scalar(L, h, F_NSEL)
         res = SearchResult(
             status=_scalar(L, h, F_STATUS),
             nodes=_get(L, h, F_RES_NODE), s_c=_get(L, h, F_RES_SC, dtype=np.int32),
             s_m=_get(L, h, F_RES_SM, dtype=np.int32), s_r=_get(L, h, F_RES_SR, dtype=np.float64),
-            central=_run(L, h, 0, n), marginal=_run(L, h, 1, n),
+            central=_run(L, h, 0, n, trace), marginal=_run(L, h, 1, n, trace),
             cg_node=_get(L, h, F_CG_NODE, 0), cg_score=_get(L, h, F_CG_SCORE, 0),
             cg_level=_get(L, h, F_CG_LEVEL, 0),
             selected=_get(L, h, F_SEL), selected_sc=_get(L, h, F_SEL_SC),
@@ -207,9 +292,31 @@ def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int
             matched=_get(L, h, F_MATCHED, dtype=np.int32),
             match_level=_get(L, h, F_MATCH_LEVEL, dtype=np.int32),
             sel_sm=_get(L, h, F_SM, dtype=np.int32),
-            vm=[_get(L, h, F_VM, 0, g_) for g_ in range(nsel)],
-            em=[_get(L, h, F_EM, 0, g_) for g_ in range(nsel)],
-            ptc=_get(L, h, F_PTC, dtype=np.int32))
+            vm=[_get(L, h, F_VM, 0, g_) for g_ in range(nsel)] if subgraphs else None,
+            em=[_get(L, h, F_EM, 0, g_) for g_ in range(nsel)] if subgraphs else None,
+            ptc=_get(L, h, F_PTC, dtype=np.int32) if subgraphs else None)
     finally:
         L.orc_free(h)
     return res
+
+
+def search_many(pg: PreparedGraph, queries, threads: int = 0, trace: bool = False,
+                subgraphs: bool = False) -> list:
+    """The oracle on many queries of one prepared graph, query-parallel over
+    ``threads`` threads (default: every host core).  Each search is the
+    serial oracle on its own state; only the graph is shared.  Queries are
+    ``rpqgen.Query``-like objects; results come back in query order."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    qs = list(queries)
+    nthreads = max(1, min(threads or (os.cpu_count() or 1), len(qs) or 1))
+
+    def one(q):
+        return search(None, None, q.central, q.marginal, q.k, q.max_depth, q.gamma,
+                      w=getattr(q, "w", 0), product=getattr(q, "product", False), prepared=pg,
+                      trace=trace, subgraphs=subgraphs)
+
+    if nthreads == 1:
+        return [one(q) for q in qs]
+    with ThreadPoolExecutor(max_workers=nthreads) as ex:
+        return list(ex.map(one, qs))

@@ -224,6 +224,8 @@ typedef struct {
     int disable_stops;        /* test only: no CF and no early termination */
     int exhaustive_marginal;  /* test only: marginal run to L / empty frontier */
     uint64_t shuffle_seed;    /* test only: nonzero shuffles frontier and neighbour order */
+    int record_frontiers;     /* keep every Q_l (the trace); off: results and counts only */
+    int subgraphs;            /* G^m and the PTC check of each RPG */
 } orc_options;
 
 /* Result identification (Section 4.2.3). */
@@ -354,15 +356,17 @@ static void explore(const orc_graph *G, const int32_t *kws, int32_t nt, int32_t 
             R->h[v * nt + j] = 0;
             F[v] = 1;
         }
-    vpush(&R->q_ptr, 0);
+    if (opt->record_frontiers) vpush(&R->q_ptr, 0);
     int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t *nbr = NULL; int64_t nbr_cap = 0;
     for (int32_t l = 0; l <= L; ++l) {
         /* Frontier enqueue: sequential scan of F, then reset F. */
         int64_t nq = 0;
         for (int32_t v = 0; v < n; ++v) if (F[v]) { Q[nq++] = v; F[v] = 0; }
-        for (int64_t i = 0; i < nq; ++i) vpush(&R->q_nodes, Q[i]);
-        vpush(&R->q_ptr, R->q_nodes.n);
+        if (opt->record_frontiers) {
+            for (int64_t i = 0; i < nq; ++i) vpush(&R->q_nodes, Q[i]);
+            vpush(&R->q_ptr, R->q_nodes.n);
+        }
         R->last_level = l;
         identify(R, mode, l, Q, nq, S, opt);
         if (terminate_run(R, mode, S, l, sp, opt) || l == L) break;
@@ -583,30 +587,57 @@ static int cmp_rec(const void *p, const void *q) {
     return (a->node > b->node) - (a->node < b->node);
 }
 
-void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *col, const uint8_t *a,
-                 int32_t n_kw, const int64_t *kw_ptr, const int32_t *kw_nodes,
-                 const int32_t *central, int32_t n_c, const int32_t *marginal, int32_t n_m,
-                 int32_t k, int32_t max_depth, double gamma, int32_t w, int32_t product,
-                 int32_t disable_stops, int32_t exhaustive_marginal, uint64_t shuffle_seed) {
+/* The graph a search reads, with the CSR transpose (the in-entries of every
+ * node, used by the recovering phase) built once.  The caller's arrays are
+ * referenced, not copied, and must outlive the handle.  Searches only read
+ * it, so several may run on one prepared graph at the same time (one thread
+ * each); every search keeps all of its own state. */
+void *orc_graph_new(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *col, const uint8_t *a,
+                    int32_t n_kw, const int64_t *kw_ptr, const int32_t *kw_nodes) {
+    if (n < 0 || m2 < 0 || n_kw < 0) return NULL;
+    orc_graph *G = (orc_graph *)calloc(1, sizeof(orc_graph));
+    *G = (orc_graph){ n, m2, row_ptr, col, a, n_kw, kw_ptr, kw_nodes, NULL, NULL, NULL };
+    G->tptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    G->tent = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m2 > 0 ? m2 : 1));
+    G->tsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m2 > 0 ? m2 : 1));
+    for (int64_t e = 0; e < m2; ++e) G->tptr[col[e] + 1]++;
+    for (int32_t v = 0; v < n; ++v) G->tptr[v + 1] += G->tptr[v];
+    {
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
+        memcpy(cur, G->tptr, sizeof(int64_t) * ((size_t)n + 1));
+        for (int32_t u = 0; u < n; ++u)
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) { G->tsrc[cur[col[e]]] = u; G->tent[cur[col[e]]++] = e; }
+        free(cur);
+    }
+    return G;
+}
+
+void orc_graph_free(void *graph) {
+    orc_graph *G = (orc_graph *)graph;
+    if (!G) return;
+    free(G->tptr); free(G->tent); free(G->tsrc);
+    free(G);
+}
+
+/* flags of orc_search_graph */
+enum { ORC_TRACE = 1, ORC_SUBGRAPHS = 2 };
+
+/* One radial-pattern query on a prepared graph.  flags: ORC_TRACE keeps every
+ * frontier Q_l; ORC_SUBGRAPHS builds G^m and checks PTC for each RPG.  The
+ * results and every other field do not depend on the flags. */
+void *orc_search_graph(const void *graph, const int32_t *central, int32_t n_c, const int32_t *marginal, int32_t n_m,
+                       int32_t k, int32_t max_depth, double gamma, int32_t w, int32_t product,
+                       int32_t disable_stops, int32_t exhaustive_marginal, uint64_t shuffle_seed, int32_t flags) {
+    const orc_graph G = *(const orc_graph *)graph;
+    const int32_t n_kw = G.n_kw;
+    const int64_t *kw_ptr = G.kw_ptr;
     orc_result *res = (orc_result *)calloc(1, sizeof(orc_result));
     res->n_c = n_c; res->n_m = n_m;
     if (n_c <= 0 || n_m < 0 || k <= 0 || max_depth < 0 || max_depth > 254 || (w != 0 && w < k)) { res->status = -1; return res; }
     for (int32_t j = 0; j < n_c; ++j) if (central[j] < 0 || central[j] >= n_kw) { res->status = -1; return res; }
     for (int32_t j = 0; j < n_m; ++j) if (marginal[j] < 0 || marginal[j] >= n_kw) { res->status = -1; return res; }
-    orc_graph G = { n, m2, row_ptr, col, a, n_kw, kw_ptr, kw_nodes, NULL, NULL, NULL };
-    G.tptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
-    G.tent = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m2 > 0 ? m2 : 1));
-    G.tsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m2 > 0 ? m2 : 1));
-    for (int64_t e = 0; e < m2; ++e) G.tptr[col[e] + 1]++;
-    for (int32_t v = 0; v < n; ++v) G.tptr[v + 1] += G.tptr[v];
-    {
-        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
-        memcpy(cur, G.tptr, sizeof(int64_t) * ((size_t)n + 1));
-        for (int32_t u = 0; u < n; ++u)
-            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) { G.tsrc[cur[col[e]]] = u; G.tent[cur[col[e]]++] = e; }
-        free(cur);
-    }
-    orc_options opt = { disable_stops, exhaustive_marginal, shuffle_seed };
+    orc_options opt = { disable_stops, exhaustive_marginal, shuffle_seed, (flags & ORC_TRACE) != 0,
+                        (flags & ORC_SUBGRAPHS) != 0 };
     /* beam width: w = k unless given (Section 3.4 uses w = k; k <= w) */
     const score_params sp = { w > 0 ? w : k, k, gamma, product };
     const int32_t wb = sp.w;
@@ -655,7 +686,7 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
         S->ptc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S->n_sel > 0 ? S->n_sel : 1));
         for (int32_t g = 0; g < S->n_sel; ++g) {
             S->ptc[g] = -1;
-            if (!S->matched[g]) continue;
+            if (!S->matched[g] || !opt.subgraphs) continue;
             recover_marginal(&G, &res->rm, &S->vc_kw[g], &S->vm[g], &S->em[g]);
             vec vr = {0, 0, 0}, er = {0, 0, 0};
             for (int64_t t = 0; t < S->vc_all[g].n; ++t) vpush(&vr, S->vc_all[g].v[t]);
@@ -694,7 +725,25 @@ void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *c
         res->res_node[i] = R[i].node; res->res_sc[i] = R[i].sc; res->res_sm[i] = R[i].sm; res->res_sr[i] = R[i].sr;
     }
     free(R);
-    free(G.tptr); free(G.tent); free(G.tsrc);
+    return res;
+}
+
+/* The same query on a graph prepared for this call alone, with the full trace
+ * and the result subgraphs. */
+void *orc_search(int32_t n, int64_t m2, const int64_t *row_ptr, const int32_t *col, const uint8_t *a,
+                 int32_t n_kw, const int64_t *kw_ptr, const int32_t *kw_nodes,
+                 const int32_t *central, int32_t n_c, const int32_t *marginal, int32_t n_m,
+                 int32_t k, int32_t max_depth, double gamma, int32_t w, int32_t product,
+                 int32_t disable_stops, int32_t exhaustive_marginal, uint64_t shuffle_seed) {
+    void *G = orc_graph_new(n, m2, row_ptr, col, a, n_kw, kw_ptr, kw_nodes);
+    if (!G) {
+        orc_result *res = (orc_result *)calloc(1, sizeof(orc_result));
+        res->status = -1;
+        return res;
+    }
+    void *res = orc_search_graph(G, central, n_c, marginal, n_m, k, max_depth, gamma, w, product, disable_stops,
+                                 exhaustive_marginal, shuffle_seed, ORC_TRACE | ORC_SUBGRAPHS);
+    orc_graph_free(G);
     return res;
 }
 

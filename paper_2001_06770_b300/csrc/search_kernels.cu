@@ -814,9 +814,15 @@ k_run(DevKG g, DevSlot s, int run) {
     const uint32_t l = *(volatile uint32_t*)&c->lvl_enq;
     if (blockIdx.x == 0 && threadIdx.x == 0) { c->lvl_exp = l; c->iters[run] += 1; }
     enqueue_level<true>(g, s, run, l);
-    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) return;
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) break;
     if (expand_level<true>(g, s, run, l, 0, 0)) return;
-    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) return;
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) break;
+  }
+  // a barrier ran out: the run ends without results; the error reaches the
+  // slot's sticky word (read by rpq_sync_device) as well as the control block
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->done = 1;
+    atomicOr(s.sticky, __ldcg(&c->err));
   }
 }
 

@@ -72,8 +72,9 @@ def test_batch_equals_one_at_a_time(bundle):
         assert status == 0
         one, st1 = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
         assert res.tobytes() == one.tobytes()
-        # the launch count differs by design: slot 0 runs each level loop as one
-        # persistent kernel, batch slots launch a kernel pair per level
+        # the launch count depends on the launch mode (under RPQ_PERSISTENT=1
+        # slot 0 runs each level loop as one persistent kernel, batch slots
+        # never do), so only the search statistics must agree
         st.pop("kernels"), st1.pop("kernels")
         assert st == st1
 
