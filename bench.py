@@ -1,20 +1,28 @@
 """Benchmark of the B300 radial-pattern keyword search (one JSON line on stdout).
 
-Workload (N = 1): the medium synthetic knowledge graph - R-MAT
-(a=.57, b=.19, c=.19), 2^21 nodes, 2^25 sampled edges, int32 CSR both
-directions - with 64 queries issued one at a time (|C| in 2..4, |M| in 0..4,
-keyword ranks 100..20,000, k = 20, max depth 8).  One step = the 64 queries.
+Workload (N = 1, default): the large open-KG-shaped graph - Chung-Lu
+(exponent 2.1), 5e7 nodes, 4e8 sampled edges (7.6e8 CSR entries, maximum
+degree 638,167), int32 CSR both directions, Zipf(1.0) keywords over a 5M-word
+vocabulary - with 256 queries issued one at a time (|C| = |M| = 3, keyword
+ranks 100..20,000, k = 20, max depth 8).  One step = the 256 queries.
 
   value      queries/s with the query keyword ids already in device memory and
              results left there (rpq_search_device, CUDA graph per shape),
-             CUDA events on the library's stream, L2 flushed between steps
+             CUDA events on the library's stream; the 3 GB adjacency is larger
+             than L2 and L2 is also flushed between steps
   e2e        the same through rpq_search (host buffers in and out, one
              synchronous call per query), wall clock
+  batched    the batched workload's mix (uneven shapes, head and tail
+             keywords) on the same graph through rpq_search_batch, against the
+             same queries one at a time, results compared
   roofline   the expansion kernel: algorithmic bytes / its device time,
              measured with CUDA events around each launch (profiling pass)
-  cpu_baseline  the serial CPU oracle on a bounded sample of the workload
+  cpu_baseline  the serial CPU oracle on a sample of the workload, one query
+             per host core (threads sharing one prepared graph); every
+             sampled result is compared with the GPU's (oracle_checked)
 
 ``--impl reference`` times the CPU oracle itself as the reference arm.
+``--workload medium|batched|served`` runs the other configurations.
 Multi-GPU (torchrun): queries are independent, every rank runs its own copy
 of the workload on its GPU (replicas, no collective on the data path).
 """
@@ -38,6 +46,9 @@ sys.path.insert(0, ROOT)
 METRIC = "RPQ queries/sec and GTEPS (batched vs one-at-a-time, bit-exact); p50/p99 latency"
 WORKLOAD = ("medium: R-MAT(.57,.19,.19) 2^21 nodes, 2^25 sampled edges, symmetric int32 CSR; "
             "64 RPQs one at a time, |C| 2-4, |M| 0-4, ranks 100-20000, k=20, L=8")
+WORKLOAD_LARGE = ("large: Chung-Lu (exponent 2.1) 5e7 nodes, 4e8 sampled edges, symmetric int32 CSR; "
+                  "256 RPQs one at a time, |C| = |M| = 3, ranks 100-20000, k=20, L=8")
+REL_TOL = 1e-6   # S^r; node ids, S^c and S^m must be equal
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
 # DRAM bytes per expansion launch from one ncu capture (dram__bytes_read.sum +
@@ -155,55 +166,69 @@ def host_cpu() -> dict:
     return {"nproc": os.cpu_count(), "model": model}
 
 
-def oracle_sample(ds, qs, n, act=None, budget_s=20.0):
-    """Serial oracle on the first n queries, stopping early once budget_s
-    seconds are spent (at least one query): (queries/s, seconds, queries)."""
-    import oracle
-    if n <= 0:
-        return None, 0.0, 0
-    if act is None:
-        act = oracle.dataset_activation(ds)
-    t = time.perf_counter()
-    done = 0
-    for q in qs[:n]:
-        oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
-        done += 1
-        if time.perf_counter() - t >= budget_s:
-            break
-    dt = time.perf_counter() - t
-    return done / dt, dt, done
+def same_results(res, orc) -> bool:
+    """A GPU result array equals the oracle's: node ids, S^c and S^m exactly,
+    S^r within REL_TOL relative, same count and order."""
+    return (len(res) == len(orc.nodes) and res["node"].tolist() == [int(x) for x in orc.nodes]
+            and res["s_c"].tolist() == orc.s_c.tolist() and res["s_m"].tolist() == orc.s_m.tolist()
+            and bool(np.allclose(res["s_r"], orc.s_r, rtol=REL_TOL, atol=0)))
 
 
-def _oracle_worker(args):
-    """One process of the query-parallel oracle: its share of the queries,
-    timed after the dataset and activation levels are ready."""
-    ds_name, qs, budget_s = args
-    sys.path.insert(0, ROOT)
-    import oracle
-    import rpqgen
-    ds = rpqgen.make_dataset(ds_name)
-    act = oracle.dataset_activation(ds)
-    t = time.perf_counter()
-    done = 0
-    for q in qs:
-        oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
-        done += 1
-        if time.perf_counter() - t >= budget_s:
-            break
-    return done, time.perf_counter() - t
+class OracleLeg:
+    """The serial CPU oracle on one dataset: its activation levels and the
+    graph's transpose are built once (outside any timed region), then
+    queries run one per thread on the host cores (each search is the serial
+    oracle; the ctypes calls release the GIL, so the threads run in parallel
+    and share one copy of the graph)."""
+
+    def __init__(self, ds):
+        import oracle
+        t = time.perf_counter()
+        self.act = oracle.dataset_activation(ds, detail=False)
+        self.pg = oracle.PreparedGraph(ds, self.act.a)
+        self.setup_s = time.perf_counter() - t
+
+    def run(self, qs, threads=0):
+        """(results, per-query seconds, wall seconds, threads) of the queries,
+        query-parallel over `threads` threads (default: every host core)."""
+        import oracle
+        from concurrent.futures import ThreadPoolExecutor
+        qs = list(qs)
+        threads = max(1, min(threads or (os.cpu_count() or 1), max(len(qs), 1)))
+
+        def one(q):
+            t = time.perf_counter()
+            r = oracle.search(None, None, q.central, q.marginal, q.k, q.max_depth, q.gamma,
+                              w=getattr(q, "w", 0), product=getattr(q, "product", False), prepared=self.pg,
+                              trace=False, subgraphs=False)
+            return r, time.perf_counter() - t
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            out = list(ex.map(one, qs))
+        wall = time.perf_counter() - t0
+        return [r for r, _ in out], [d for _, d in out], wall, threads
+
+    def check(self, qs, gpu_results, what="", threads=0):
+        """Run the oracle on `qs` and assert that every GPU result equals it;
+        returns the cpu_baseline record of that run."""
+        res, per_q, wall, threads = self.run(qs, threads)
+        for i, (g, o) in enumerate(zip(gpu_results, res)):
+            if not same_results(g, o):
+                raise AssertionError(f"{what} query {i}: GPU {g.tolist()} != oracle {list(zip(o.nodes.tolist(), o.s_c.tolist(), o.s_m.tolist(), o.s_r.tolist()))}")
+        return {"value": len(qs) / wall, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                "per_query_s": {"mean": float(np.mean(per_q)), "max": float(np.max(per_q))},
+                "wall_s": wall, "setup_s": self.setup_s}
+
+    def close(self):
+        self.pg.close()
 
 
-def oracle_parallel_sample(ds_name, qs, per_core=2, budget_s=20.0):
-    """The oracle query-parallel over all host cores, one process per core
-    (spawned, so no CUDA state is inherited): (queries/s, processes, queries)."""
-    import multiprocessing as mp
-    cores = os.cpu_count() or 1
-    shares = [(ds_name, qs[i::cores][:per_core], budget_s) for i in range(cores)]
-    shares = [sh for sh in shares if sh[1]]
-    with mp.get_context("spawn").Pool(len(shares)) as pool:
-        out = pool.map(_oracle_worker, shares)
-    done = sum(d for d, _ in out)
-    return done / max(t for _, t in out), len(shares), done
+def sample_indices(n, count):
+    """`count` query indices spread evenly over n (all of them if count >= n)."""
+    if count >= n:
+        return list(range(n))
+    return sorted(set(int(round(i * (n - 1) / max(count - 1, 1))) for i in range(count)))
 
 
 def raks_cpu_sample(ds, qs, n, budget_s=20.0):
@@ -224,30 +249,35 @@ def raks_cpu_sample(ds, qs, n, budget_s=20.0):
 
 
 def run_reference(args):
+    """The reference arm: the serial CPU oracle itself on this workload's
+    queries, one query per host core at a time (threads sharing one prepared
+    graph).  A step is one query of the workload (cycling through them); the W
+    warm-up queries run first, then the K timed ones, each wave as wide as the
+    host has cores."""
     ws, rank, _ = dist_init()
     if rank != 0:
         return 0
-    import oracle
     import rpqgen
     wl = WORKLOADS[args.workload]
     ds = rpqgen.make_dataset(wl["ds"])
     qs = rpqgen.workload_queries(wl["queries"], ds)
-    act = oracle.dataset_activation(ds)
-    times = []
-    for s in range(args.warmup + args.steps):
-        q = qs[s % len(qs)]
-        t = time.perf_counter()
-        oracle.search(ds, act.a, q.central, q.marginal, q.k, q.max_depth, q.gamma)
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t)
-    total = sum(times)
-    qps = args.steps / total
+    leg = OracleLeg(ds)
+    order = [qs[i % len(qs)] for i in range(args.warmup + args.steps)]
+    leg.run(order[:args.warmup])
+    _, per_q, wall, threads = leg.run(order[args.warmup:])
+    leg.close()
+    qps = args.steps / wall
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": wl["desc"], "step": "one query of the workload (cycling)"},
-            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} queries of the {len(qs)}, serial C oracle, one core"},
+            "config": {"workload": wl["desc"], "step": "one query of the workload (cycling), "
+                       f"{threads} queries at a time on {threads} host threads"},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} timed queries of the {len(qs)} after {args.warmup} warm-up "
+                                       f"queries, serial C oracle, one query per thread on {threads} threads "
+                                       f"sharing one prepared graph (set-up {leg.setup_s:.0f} s untimed)",
+                             "per_query_s": {"mean": float(np.mean(per_q)), "max": float(np.max(per_q))}},
+            "host_cpu": host_cpu(),
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -257,9 +287,10 @@ WORKLOADS = {
     "medium": dict(ds="medium", queries="medium", mode="single", desc=WORKLOAD),
     "tiny": dict(ds="tiny", queries="tiny", mode="single",
                  desc="tiny: R-MAT 2^14 nodes, one RPQ (smoke and multi-process checks, not a bench line)"),
-    "large": dict(ds="large", queries="large", mode="single",
-                  desc="large: Chung-Lu (exponent 2.1) 5e7 nodes, 4e8 sampled edges, symmetric int32 CSR; "
-                       "256 RPQs one at a time, |C| = |M| = 3, ranks 100-20000, k=20, L=8"),
+    "large": dict(ds="large", queries="large", mode="single", desc=WORKLOAD_LARGE),
+    "cl_5m": dict(ds="cl_5m", queries="cl_5m", mode="single",
+                  desc="cl_5m: Chung-Lu (exponent 2.1) 5e6 nodes, 4e7 sampled edges; the large workload's "
+                       "queries (profiling case, not a bench line)"),
     "batched": dict(ds="large", queries="batched", mode="batch",
                     desc="batched: large graph; 4096 RPQs of uneven shape (|C| 2-6, |M| 0-8, head/tail keywords, "
                          "k in {5,10,20}, L=8) in one rpq_search_batch call"),
@@ -269,35 +300,67 @@ WORKLOADS = {
 }
 
 
+DENSE_UNITS = 1 << 20   # a Glevel with at least this many work units (4 MB of adjacency) counts as dense
+
+
+def level_bytes(r, n):
+    """Algorithmic bytes of one Glevel (a record of rpq_profile_levels) for
+    the expansion and for the frontier enqueue.  Expansion: 4 per work unit
+    (the packed CSR entry), 1 per (column, edge) activation executed (the
+    neighbour's visited byte), 2 per claim written (level byte and visited
+    bit), 10 per item (record and column mask).  Enqueue: the frontier read
+    (the n-bit bit map, or 4 bytes per queued node), per frontier node its
+    row bounds (8), two level-index entries (4), its visited byte and one
+    level byte per column, and the items and warp-tile starts it writes."""
+    exp = 4 * r["units"] + r["e_act"] + 2 * r["claims"] + 10 * r["items"]
+    fr = r["frontier"]
+    scan = 4 * fr if r["flags"] & 8 else (n + 7) // 8
+    enq = scan + fr * (13 + r["columns"]) + 10 * r["items"] + 4 * ((r["units"] + 127) // 128)
+    return exp, enq
+
+
 def expand_roofline(kg, qs, stats, workload="medium"):
-    """Profiling pass: device time of each kernel class, and the expansion
-    kernel's algorithmic bytes per second against the measured HBM peak.  The
-    stored ncu DRAM traffic applies to the medium workload's 64 queries only."""
+    """Profiling pass (kernels launched directly, CUDA events around each
+    launch): device time per kernel class, and per Glevel the algorithmic
+    bytes of the expansion and the enqueue against the measured HBM peak -
+    over all launches, and over the dense levels alone.  The stored ncu DRAM
+    traffic applies to the medium workload's 64 queries only."""
     kg.set_profiling(True)
+    kg.profile(reset=True)
+    kg.profile_levels(reset=True)
     for q in qs:
         kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
     prof = kg.profile(reset=True)
+    recs = kg.profile_levels(reset=True)
     kg.set_profiling(False)
-    exp_ms, exp_launches = prof["expand"]
-    units = sum(s["work_units"] for s in stats)
-    items = sum(s["work_items"] for s in stats)
-    hits = sum(s["hits_central"] + s["hits_marginal"] for s in stats)
-    # activations the expansion kernel executed (E_act less the skipped final marginal levels)
-    e_act = sum(s["e_act_central"] + s["e_act_marginal"] - s["e_act_skipped"] for s in stats)
-    alg_bytes = 4 * units + e_act + 2 * hits + 10 * items      # adjacency, level checks, writes, items
-    achieved = alg_bytes / (exp_ms / 1e3) / 1e9 if exp_ms > 0 else 0.0
     peak, peak_kind = hbm_peak()
+    exp_ms, exp_launches = prof["expand"]
+    total_ms = sum(v[0] for v in prof.values())
+
+    def agg(rows, kind):
+        ms = sum(r[f"{kind}_ms"] for r in rows)
+        by = sum(level_bytes(r, kg.n)[0 if kind == "expand" else 1] for r in rows)
+        ach = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"launches": len(rows), "ms": ms, "alg_bytes": by, "achieved": ach, "frac": ach / peak,
+                "alg_bytes_per_launch": by / max(len(rows), 1), "avg_launch_us": 1e3 * ms / max(len(rows), 1)}
+
+    expanded = [r for r in recs if r["flags"] & 1]
+    dense = [r for r in expanded if r["units"] >= DENSE_UNITS]
+    e_all, e_dense, q_all = agg(expanded, "expand"), agg(dense, "expand"), agg(recs, "enqueue")
+    q_dense = agg([r for r in recs if r["frontier"] >= (1 << 18)], "enqueue")
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if workload == "medium" and len(qs) == 64 and NCU_TRAFFIC["sha1"] == expand_source_sha() else None)
-    total_ms = sum(v[0] for v in prof.values())
-    avg_s = exp_ms / 1e3 / max(exp_launches, 1)
+    avg_s = e_all["ms"] / 1e3 / max(e_all["launches"], 1)
     dram_gbs = traffic / avg_s / 1e9 if traffic and avg_s > 0 else None
-    roof = {"bound": "hbm", "kernel": "k_expand", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+    roof = {"bound": "hbm", "kernel": "k_expand", "achieved": e_all["achieved"], "peak": peak, "unit": "GB/s",
+            "frac": e_all["frac"], "traffic": traffic, "peak_kind": peak_kind,
             "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
-            "alg_bytes_per_launch": alg_bytes / max(exp_launches, 1),
-            "avg_launch_us": 1e3 * exp_ms / max(exp_launches, 1), "launches": exp_launches,
-            "share_of_device_time": exp_ms / total_ms if total_ms else None}
+            "alg_bytes_per_launch": e_all["alg_bytes_per_launch"], "avg_launch_us": e_all["avg_launch_us"],
+            "launches": e_all["launches"], "share_of_device_time": exp_ms / total_ms if total_ms else None,
+            "dense": dict(e_dense, units_min=DENSE_UNITS,
+                          share_of_expand_time=e_dense["ms"] / e_all["ms"] if e_all["ms"] else None),
+            "enqueue": dict(q_all, kernel="k_enqueue", dense=dict(q_dense, frontier_min=1 << 18),
+                            share_of_device_time=prof["enqueue"][0] / total_ms if total_ms else None)}
     return roof, {k: v[0] for k, v in prof.items()}
 
 
@@ -413,13 +476,25 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
     batched = ws * nq * args.steps / t_b
 
     roof, kms = expand_roofline(kg, qs, stats, args.workload)
+    # the batched workload's mix on the same graph (large only): one batch
+    # call against the same queries one at a time, results compared
+    mix = batched_mix(args, ws, ds, kg) if args.workload == "large" and args.mix_queries else None
     if rank != 0:
         return None
-    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
-    mc = raks_cpu_sample(ds, qs, args.cpu_sample * 2) if args.cpu_sample else None
-    # query-parallel oracle on every host core (one process each) where a
-    # process's copy of the graph is small enough (not on the 50M-node graph)
-    par = oracle_parallel_sample(wl["ds"], qs) if args.cpu_sample and kg.n <= (1 << 22) else None
+    # the oracle on a sample of the queries (one per host core, or all of
+    # them on the medium graph); every sampled GPU result must equal it
+    cores = os.cpu_count() or 1
+    n_check = args.cpu_sample if args.cpu_sample >= 0 else (nq if kg.n <= (1 << 22) else max(8, cores))
+    idx = sample_indices(nq, n_check)
+    leg = OracleLeg(ds)
+    cpu = leg.check([qs[i] for i in idx], [host_res[i] for i in idx], "one-at-a-time")
+    checked = {"one_at_a_time": len(idx)}
+    if mix is not None:
+        midx = sample_indices(len(mix["queries"]), max(4, cores // 2))
+        leg.check([mix["queries"][i] for i in midx], [mix["results"][i] for i in midx], "batched mix")
+        checked["batched_mix"] = len(midx)
+    leg.close()
+    mc = raks_cpu_sample(ds, qs, 8) if args.raks_cpu else None
     line = base_line(args, ws, wl, value, t_dev / args.steps, args.steps)
     line.update({
         "config": {"workload": wl["desc"], "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
@@ -428,26 +503,48 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
         "e_act_per_step": e_act,
         "e_act_skipped_per_step": sum(s["e_act_skipped"] for s in stats),
         "batched_qps": batched,
+        "batched_mix": None if mix is None else {k: v for k, v in mix.items() if k not in ("queries", "results")},
         "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roof,
         "kernel_ms_per_step": kms,
-        "cpu_baseline": ({"value": par[0], "unit": "queries/s", "cores": par[1], "kind": "oracle",
-                          "sample": f"{par[2]} of the {nq} queries dealt round-robin to {par[1]} oracle "
-                                    f"processes (one per core), throughput over the slowest process"}
-                         if par else
-                         {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                          "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"}),
+        "oracle_checked": checked,
+        "cpu_baseline": dict(cpu, sample=f"{len(idx)} of the {nq} queries (evenly spaced), serial C oracle, "
+                                         f"one query per thread on {cpu['cores']} threads sharing one prepared "
+                                         f"graph; wall {cpu['wall_s']:.1f} s, set-up {cpu['setup_s']:.0f} s "
+                                         f"untimed; every result equal to the GPU's"),
         "host_cpu": host_cpu(),
-        "cpu_baseline_one_core": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                                  "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
         "raks_cpu": None if mc is None else {
             "value": mc[0], "unit": "queries/s", "threads": mc[3], "kind": "paper's multi-core CPU search (OpenMP)",
             "sample": f"first {mc[2]} of the {nq} queries, {mc[1]:.1f} s"},
         "clocks": clk,
     })
     return line
+
+
+def batched_mix(args, ws, ds, kg):
+    """The first `--mix-queries` queries of the batched workload (uneven
+    shapes, head and tail keywords) on the loaded graph: one rpq_search_batch
+    call against the same queries one at a time; every result must agree."""
+    import rpqgen
+    mq = rpqgen.workload_queries("batched", ds)[:args.mix_queries]
+    out = kg.search_batch(mq)                                   # warm-up and results
+    assert all(st == 0 for _, _, st in out), "batch query failed"
+    barrier(ws)
+    t0 = time.perf_counter()
+    out = kg.search_batch(mq)
+    t_b = allmax(ws, time.perf_counter() - t0)
+    barrier(ws)
+    t0 = time.perf_counter()
+    one = [kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)[0] for q in mq]
+    t_1 = allmax(ws, time.perf_counter() - t0)
+    for i, (r, (b, _, _)) in enumerate(zip(one, out)):
+        assert r.tobytes() == b.tobytes(), f"batched result differs from one-at-a-time on mix query {i}"
+    return {"queries_per_call": len(mq), "batched_qps": ws * len(mq) / t_b, "one_at_a_time_qps": ws * len(mq) / t_1,
+            "batched_vs_one_at_a_time": t_1 / t_b, "equal_results_checked": len(mq),
+            "e_act": sum(st["e_act_central"] + st["e_act_marginal"] for _, st, _ in out),
+            "queries": mq, "results": one}
 
 
 def run_batch(args, ws, rank, local, wl, ds, qs, kg):
@@ -479,7 +576,11 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
     roof, kms = expand_roofline(kg, [qs[i] for i in sample], sstats, args.workload)
     if rank != 0:
         return None
-    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    cores = os.cpu_count() or 1
+    idx = sample_indices(nq, args.cpu_sample if args.cpu_sample >= 0 else max(8, cores))
+    leg = OracleLeg(ds)
+    cpu = leg.check([qs[i] for i in idx], [out[i][0] for i in idx], "batched")
+    leg.close()
     line = base_line(args, ws, wl, value, t / args.steps, args.steps)
     line.update({
         "config": {"workload": wl["desc"], "queries_per_step": nq, "n": kg.n, "m2": kg.m2, "abar": ds.abar,
@@ -492,8 +593,10 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
                 "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
         "gpu_launches": sum(s["kernels"] for s in stats) * args.steps,
         "roofline": roof, "kernel_ms_per_step_sample": kms,
-        "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
+        "oracle_checked": {"batched": len(idx)},
+        "cpu_baseline": dict(cpu, sample=f"{len(idx)} of the {nq} queries (evenly spaced), serial C oracle, "
+                                         f"one query per thread on {cpu['cores']} threads sharing one prepared "
+                                         f"graph; wall {cpu['wall_s']:.1f} s; every result equal to the GPU's"),
         "clocks": clk,
     })
     return line
@@ -507,7 +610,6 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
     import rpqgen
     nq = len(qs)
     srv = rpq.Server(kg, budget_bytes=16 << 30, max_slots=256)
-    info = srv.info()
     sample = list(range(0, nq, max(1, nq // 64)))
     alone = {i: kg.search(qs[i].central, qs[i].marginal, qs[i].k, qs[i].max_depth, qs[i].gamma)[0] for i in sample}
     t0 = time.perf_counter()
@@ -519,12 +621,16 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
     per_rate = []
     clocks = Clocks(local)
     clocks.start()
+    served = {}
+
     def serve_at(rate, below=False):
         arr = rpqgen.poisson_arrivals(nq, rate, seed=7)
         res, lat, status, wall = srv.replay(qs, arr)
         assert (status == 0).all()
         for i in sample:
             assert res[i].tobytes() == alone[i].tobytes(), f"served result differs from alone on query {i}"
+        if not served:
+            served.update({i: res[i] for i in sample})
         per_rate.append({"rate_per_s": rate, "qps": nq / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                          "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": wall,
                          "below_capacity": below})
@@ -537,16 +643,20 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
     for f in (0.5, 0.8):
         serve_at(round(f * cap), below=True)
     clk = clocks.stop()
+    srv_info = srv.info()           # pools, and the most queries that ran at once
     srv.close()
     if rank != 0:
         return None
     best = max((r for r in per_rate if not r["below_capacity"]), key=lambda r: r["qps"])
-    cpu_qps, cpu_s, cpu_n = oracle_sample(ds, qs, args.cpu_sample)
+    # the served results of the sampled queries against the oracle
+    leg = OracleLeg(ds)
+    cpu = leg.check([qs[i] for i in sample], [served[i] for i in sample], "served")
+    leg.close()
     line = base_line(args, ws, wl, ws * best["qps"], best["wall_s"], 1)
     line.update({
-        "config": {"workload": wl["desc"], "queries": nq, "n": kg.n, "m2": kg.m2, "slots": info["slots"],
-                   "slot_bytes": info["slot_bytes"], "budget_bytes": 16 << 30, "l2": "inputs larger than L2",
-                   "parallelism": f"replicas x{ws}"},
+        "config": {"workload": wl["desc"], "queries": nq, "n": kg.n, "m2": kg.m2, "budget_bytes": 16 << 30,
+                   "l2": "inputs larger than L2", "parallelism": f"replicas x{ws}"},
+        "server": {k: v for k, v in srv_info.items() if k not in ("running", "waiting")},
         "per_rate": per_rate,
         "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"]},
         "one_at_a_time_qps": one_qps,
@@ -555,8 +665,10 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
         "e2e": {"value": ws * best["qps"], "unit": "queries/s", "h2d_bytes_per_step": 88 * nq,
                 "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
         "gpu_launches": None, "roofline": None,
-        "cpu_baseline": {"value": cpu_qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {cpu_n} of the {nq} queries, serial C oracle, {cpu_s:.1f} s"},
+        "oracle_checked": {"served": len(sample)},
+        "cpu_baseline": dict(cpu, sample=f"{len(sample)} of the {nq} queries (evenly spaced), serial C oracle, "
+                                         f"one query per thread on {cpu['cores']} threads sharing one prepared "
+                                         f"graph; wall {cpu['wall_s']:.1f} s; every served result equal to it"),
         "clocks": clk,
     })
     return line
@@ -568,9 +680,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rpq", choices=["rpq", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=4)
-    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
-                    help="medium (default, the benchmark line), large, batched or served")
+    ap.add_argument("--cpu-sample", type=int, default=-1,
+                    help="queries the oracle checks (-1: every query on medium, one per host core on large)")
+    ap.add_argument("--raks-cpu", type=int, default=1, help="time the paper's OpenMP CPU search on 8 queries")
+    ap.add_argument("--mix-queries", type=int, default=512,
+                    help="large workload: queries of the batched mix run batched and one at a time")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
+                    help="large (default, the benchmark line), medium, batched or served")
     ap.add_argument("--queries", type=int, default=0, help="use only the first Q queries of the workload")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's autotuner first (1) or not (0)")
     ap.add_argument("--tune-queries", type=int, default=16, help="queries of the workload the autotuner times")

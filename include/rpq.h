@@ -356,14 +356,56 @@ typedef struct {
 int rpq_set_profiling(rpq_kg *kg, int32_t enable);
 int rpq_profile_read(rpq_kg *kg, rpq_profile *out, int32_t reset);
 
+/* Per-Glevel profile of the searches run while profiling is enabled: one
+ * record per (query, run, Glevel) whose level kernels ran before the run
+ * stopped, in launch order, with the device times of the level's frontier
+ * enqueue (Section 4.2.2-4.2.3), V_C check and expansion (Algorithm 1), and
+ * the level's work: |Q_l|, the expansion's work units (CSR entries of the
+ * newly active segments) and items, the (column, edge) activations it
+ * executed (its share of E_act) and the (node, column) claims it wrote
+ * (h = l+1; racing writers of one pair each count).  rpq_profile_levels
+ * copies up to `cap` records into `out` (caller-owned), sets *n_out to the
+ * number held (which may exceed cap) and, with reset != 0, clears them.
+ * Without profiling *n_out = 0.  Errors: RPQ_EINVAL (NULL n_out, cap < 0,
+ * NULL out with cap > 0). */
+#define RPQ_LVL_EXPANDED 1   /* the expansion ran */
+#define RPQ_LVL_SKIPPED  2   /* the V_C check showed the expansion cannot change the results */
+#define RPQ_LVL_STOP     4   /* the run stopped at this Glevel (no expansion) */
+#define RPQ_LVL_QUEUE    8   /* the enqueue read the frontier queue, not the bit map */
+typedef struct {
+    int32_t run;            /* 0 central, 1 marginal */
+    int32_t level;          /* Glevel l */
+    int32_t flags;          /* RPQ_LVL_* */
+    int32_t frontier;       /* |Q_l| */
+    int32_t columns;        /* keyword columns of the run (|C| or |M|) */
+    int32_t reserved;
+    int64_t units, items, e_act, claims;
+    double enqueue_ms, target_ms, expand_ms;
+} rpq_level_profile;
+int rpq_profile_levels(rpq_kg *kg, rpq_level_profile *out, int32_t cap, int32_t *n_out, int32_t reset);
+
 /* --------------------------------------------------------------- serving */
-/* A server runs queries with continuous batching: it owns search slots (the
- * device state of one in-flight query each, about 60 bytes per graph node
- * plus the work lists), as many as fit budget_bytes (at least one, at most
- * max_slots).  A submitted query is admitted as soon as a slot is free and
- * otherwise waits in arrival order; queries in different slots run
- * concurrently on the device, each on its own stream.  Each query runs the
- * same kernels as rpq_search, so its results equal those of rpq_search. */
+/* A server runs queries with continuous batching (the serving pattern of
+ * the problem statement, Section 4.1's server-side engine).  It owns search
+ * slots, each the keyword-independent device state of one in-flight query
+ * (visited bytes, frontier bit maps, work lists: about 45 bytes per graph
+ * node, reported as slot_bytes) with its own stream, and two pools of column
+ * pages: Node-Keyword Matrix pages (one byte per node: one hit-level column)
+ * and recovery pages (12 bytes per node: the CG masks and node list of one
+ * central column in Algorithm 2).  A query is admitted by its own hit-table
+ * memory: it needs a free slot, max(|C|, |M|) matrix pages and |C| recovery
+ * pages, which it holds until it completes; a query that does not fit waits,
+ * and waiting queries are admitted in arrival order.  Queries in different
+ * slots run concurrently on the device.  Each query runs the same kernels as
+ * rpq_search, so its results equal those of rpq_search.
+ *
+ * rpq_server_create sizes the server from budget_bytes (checked before any
+ * allocation): slots of slot_bytes with 6 matrix pages each and recovery
+ * pages with the rest (at most 8 per slot), i.e. sized for queries of about
+ * 4 central and 6 columns on average; at least one slot and 8 pages of each
+ * kind are always created (every query fits), at most max_slots slots.
+ * rpq_server_create_sized takes the counts directly (n_slots in [1, 4096],
+ * pages in [8, 2^20]).  Errors: RPQ_EINVAL, RPQ_ENOMEM, RPQ_ECUDA. */
 typedef struct rpq_server rpq_server;
 
 typedef struct {
@@ -376,8 +418,13 @@ typedef struct {
 } rpq_completion;
 
 int rpq_server_create(rpq_kg *kg, int64_t budget_bytes, int32_t max_slots, rpq_server **out);
+int rpq_server_create_sized(rpq_kg *kg, int32_t n_slots, int32_t h_pages, int32_t r_pages, rpq_server **out);
 int rpq_server_info(const rpq_server *srv, int32_t *n_slots, int64_t *slot_bytes, int32_t *n_running,
                     int32_t *n_waiting);
+/* Page pools of a server and the most queries it has had running at once.
+ * Any output pointer may be NULL. */
+int rpq_server_pages(const rpq_server *srv, int32_t *h_pages, int64_t *h_page_bytes, int32_t *r_pages,
+                     int64_t *r_page_bytes, int32_t *peak_running);
 /* Validate and enqueue one query (copied); admits it at once when a slot is
  * free.  Never waits for the device. */
 int rpq_server_submit(rpq_server *srv, const rpq_query *q, uint64_t tag);

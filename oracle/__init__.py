@@ -207,21 +207,21 @@ def _scalar(L, h, field, r=0, dtype=np.int32):
     return int(out[0])
 
 
-def _run(L, h, r, n, trace=True) -> RunTrace | None:
+def _run(L, h, r, n, trace=True, tables=True) -> RunTrace | None:
     if not _scalar(L, h, F_RAN, r):
         return None
-    if not trace:       # counts only: no hit-level table, stop levels or frontiers
-        return RunTrace(h=None, stop=None, frontiers=None, last_level=_scalar(L, h, F_LAST_LEVEL, r),
-                        last_expanded=_scalar(L, h, F_LAST_EXPANDED, r),
-                        e_act=_scalar(L, h, F_EACT, r, np.int64), new_hits=_scalar(L, h, F_NEWHITS, r, np.int64))
-    nt = L.orc_get_h(h, r, None, None, n)
-    H = np.empty((n, max(nt, 1)), np.uint8)
-    stop = np.empty(n, np.uint8)
-    L.orc_get_h(h, r, _p(H), _p(stop), n)
-    qptr = _get(L, h, F_QPTR, r)
-    qn = _get(L, h, F_QNODES, r)
-    fr = [qn[qptr[i]:qptr[i + 1]] for i in range(len(qptr) - 1)]
-    return RunTrace(h=H[:, :nt], stop=stop, frontiers=fr, last_level=_scalar(L, h, F_LAST_LEVEL, r),
+    H = stop = fr = None
+    if tables:          # hit-level table and stop levels
+        nt = L.orc_get_h(h, r, None, None, n)
+        H = np.empty((n, max(nt, 1)), np.uint8)
+        stop = np.empty(n, np.uint8)
+        L.orc_get_h(h, r, _p(H), _p(stop), n)
+        H = H[:, :nt]
+    if trace:           # every frontier Q_l
+        qptr = _get(L, h, F_QPTR, r)
+        qn = _get(L, h, F_QNODES, r)
+        fr = [qn[qptr[i]:qptr[i + 1]] for i in range(len(qptr) - 1)]
+    return RunTrace(h=H, stop=stop, frontiers=fr, last_level=_scalar(L, h, F_LAST_LEVEL, r),
                     last_expanded=_scalar(L, h, F_LAST_EXPANDED, r),
                     e_act=_scalar(L, h, F_EACT, r, np.int64), new_hits=_scalar(L, h, F_NEWHITS, r, np.int64))
 
@@ -229,19 +229,22 @@ def _run(L, h, r, n, trace=True) -> RunTrace | None:
 def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int, gamma: float = 0.5,
            disable_stops: bool = False, exhaustive_marginal: bool = False, shuffle_seed: int = 0,
            kw_ptr=None, kw_nodes=None, w: int = 0, product: bool = False, prepared: PreparedGraph = None,
-           trace: bool = True, subgraphs: bool = True) -> SearchResult:
+           trace: bool = True, subgraphs: bool = True, tables: bool = None) -> SearchResult:
     """Run the oracle on one query.  ``ds_or_graph`` is an ``rpqgen.Dataset`` or
     an ``rpqgen.Graph`` (then pass ``kw_ptr``/``kw_nodes``).  ``w`` is the CG
     beam width (0: w = k), ``product`` selects the multiplicative S^r.
 
     With ``prepared`` (a PreparedGraph of the same graph and levels) the
     graph arguments are ignored and the transpose is not rebuilt.
-    ``trace=False`` keeps no frontiers, hit-level tables or stop levels (the
-    runs' counts and levels remain); ``subgraphs=False`` builds no G^m and
-    checks no PTC (vm, em and ptc are None).  Neither changes a result."""
+    ``trace=False`` keeps no frontiers and, unless ``tables=True``, no
+    hit-level tables or stop levels (the runs' counts and levels remain);
+    ``subgraphs=False`` builds no G^m and checks no PTC (vm, em and ptc are
+    None).  None of these changes a result."""
+    if tables is None:
+        tables = trace
     if prepared is not None:
         return _search_prepared(prepared, central, marginal, k, max_depth, gamma, disable_stops,
-                                exhaustive_marginal, shuffle_seed, w, product, trace, subgraphs)
+                                exhaustive_marginal, shuffle_seed, w, product, trace, subgraphs, tables)
     if hasattr(ds_or_graph, "graph"):
         g = ds_or_graph.graph
         kw_ptr, kw_nodes = ds_or_graph.kw_ptr, ds_or_graph.kw_nodes
@@ -260,11 +263,11 @@ def search(ds_or_graph, a: np.ndarray, central, marginal, k: int, max_depth: int
                      _p(kw_nodes), _p(c), len(c), _p(m) if len(m) else None, len(m), int(k),
                      int(max_depth), float(gamma), int(w), int(bool(product)), int(disable_stops),
                      int(exhaustive_marginal), int(shuffle_seed))
-    return _collect(L, h, n, True, True)
+    return _collect(L, h, n, True, True, True)
 
 
 def _search_prepared(pg, central, marginal, k, max_depth, gamma, disable_stops, exhaustive_marginal,
-                     shuffle_seed, w, product, trace, subgraphs) -> SearchResult:
+                     shuffle_seed, w, product, trace, subgraphs, tables) -> SearchResult:
     L = _L()
     c = np.ascontiguousarray(central, np.int32)
     m = np.ascontiguousarray(marginal, np.int32)
@@ -272,17 +275,17 @@ def _search_prepared(pg, central, marginal, k, max_depth, gamma, disable_stops, 
     h = L.orc_search_graph(pg.handle, _p(c), len(c), _p(m) if len(m) else None, len(m), int(k), int(max_depth),
                            float(gamma), int(w), int(bool(product)), int(disable_stops),
                            int(exhaustive_marginal), int(shuffle_seed), flags)
-    return _collect(L, h, pg.n, trace, subgraphs)
+    return _collect(L, h, pg.n, trace, subgraphs, tables)
 
 
-def _collect(L, h, n, trace, subgraphs) -> SearchResult:
+def _collect(L, h, n, trace, subgraphs, tables) -> SearchResult:
     try:
         nsel = _scalar(L, h, F_NSEL)
         res = SearchResult(
             status=_scalar(L, h, F_STATUS),
             nodes=_get(L, h, F_RES_NODE), s_c=_get(L, h, F_RES_SC, dtype=np.int32),
             s_m=_get(L, h, F_RES_SM, dtype=np.int32), s_r=_get(L, h, F_RES_SR, dtype=np.float64),
-            central=_run(L, h, 0, n, trace), marginal=_run(L, h, 1, n, trace),
+            central=_run(L, h, 0, n, trace, tables), marginal=_run(L, h, 1, n, trace, tables),
             cg_node=_get(L, h, F_CG_NODE, 0), cg_score=_get(L, h, F_CG_SCORE, 0),
             cg_level=_get(L, h, F_CG_LEVEL, 0),
             selected=_get(L, h, F_SEL), selected_sc=_get(L, h, F_SEL_SC),

@@ -29,7 +29,7 @@ MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
            "rpq_trace", "rpq_search_subgraphs", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
-           "rpq_profile_read", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_info",
+           "rpq_profile_read", "rpq_profile_levels", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_create_sized", "rpq_server_info", "rpq_server_pages",
            "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
            "rpq_get_tuning", "rpq_set_tuning", "rpq_autotune",
            "rpq_strerror", "rpq_last_error"]
@@ -98,6 +98,18 @@ class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
 
+class LevelProfile(ctypes.Structure):
+    """rpq_level_profile of include/rpq.h."""
+    _fields_ = [("run", ctypes.c_int32), ("level", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("frontier", ctypes.c_int32), ("columns", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("units", ctypes.c_int64), ("items", ctypes.c_int64),
+                ("e_act", ctypes.c_int64), ("claims", ctypes.c_int64), ("enqueue_ms", ctypes.c_double),
+                ("target_ms", ctypes.c_double), ("expand_ms", ctypes.c_double)]
+
+
+LVL_EXPANDED, LVL_SKIPPED, LVL_STOP, LVL_QUEUE = 1, 2, 4, 8
+
+
 class Subgraphs(ctypes.Structure):
     """rpq_subgraphs of include/rpq.h."""
     _fields_ = [("nodes", ctypes.c_void_p), ("nodes_cap", ctypes.c_int64),
@@ -138,9 +150,12 @@ def lib():
         L.rpq_slot_stream.argtypes = [P, i32, ctypes.POINTER(P)]
         L.rpq_set_profiling.argtypes = [P, i32]
         L.rpq_profile_read.argtypes = [P, ctypes.POINTER(Profile), i32]
+        L.rpq_profile_levels.argtypes = [P, P, i32, P, i32]
         L.rpq_topk_keys_noalloc.argtypes = [P, ctypes.c_uint32, i32, P, P, P]
         L.rpq_server_create.argtypes = [P, i64, i32, ctypes.POINTER(P)]
+        L.rpq_server_create_sized.argtypes = [P, i32, i32, i32, ctypes.POINTER(P)]
         L.rpq_server_info.argtypes = [P, P, P, P, P]
+        L.rpq_server_pages.argtypes = [P, P, P, P, P, P]
         L.rpq_server_submit.argtypes = [P, ctypes.POINTER(Query), ctypes.c_uint64]
         L.rpq_server_poll.argtypes = [P, P, i32, P, i32]
         L.rpq_server_replay.argtypes = [P, P, P, i32, P, P, P, P, P]
@@ -379,19 +394,42 @@ class KG:
         _check(lib().rpq_profile_read(self._h, ctypes.byref(p), int(bool(reset))))
         return {c: (p.ms[i], p.launches[i]) for i, c in enumerate(PROF_CLASSES)}
 
+    def profile_levels(self, reset: bool = False):
+        """Per-Glevel records of the profiled searches (rpq_profile_levels):
+        a list of dicts with run, level, flags, frontier, units, items, e_act,
+        claims and the enqueue / V_C check / expansion device milliseconds."""
+        n = ctypes.c_int32()
+        _check(lib().rpq_profile_levels(self._h, None, 0, ctypes.byref(n), 0))
+        buf = (LevelProfile * max(n.value, 1))()
+        _check(lib().rpq_profile_levels(self._h, ctypes.cast(buf, ctypes.c_void_p), n.value, ctypes.byref(n),
+                                        int(bool(reset))))
+        return [{f: getattr(buf[i], f) for f, _ in LevelProfile._fields_} for i in range(n.value)]
+
 
 class Server:
     """Continuous-batching server over a loaded KG (rpq_server_* in rpq.h)."""
 
-    def __init__(self, kg: KG, budget_bytes: int, max_slots: int = 256):
+    def __init__(self, kg: KG, budget_bytes: int = 0, max_slots: int = 256, slots: int = 0, h_pages: int = 0,
+                 r_pages: int = 0):
+        """Sized from budget_bytes (rpq_server_create), or, with `slots`,
+        from explicit slot and page counts (rpq_server_create_sized)."""
         self._h = ctypes.c_void_p()
         self.kg = kg
-        _check(lib().rpq_server_create(kg._h, int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
+        if slots:
+            _check(lib().rpq_server_create_sized(kg._h, int(slots), int(h_pages), int(r_pages),
+                                                 ctypes.byref(self._h)))
+        else:
+            _check(lib().rpq_server_create(kg._h, int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
 
     def info(self):
         n, b, r, w = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib().rpq_server_info(self._h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(r), ctypes.byref(w)))
-        return dict(slots=n.value, slot_bytes=b.value, running=r.value, waiting=w.value)
+        hp, hb, rp, rb, pk = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().rpq_server_pages(self._h, ctypes.byref(hp), ctypes.byref(hb), ctypes.byref(rp), ctypes.byref(rb),
+                                      ctypes.byref(pk)))
+        return dict(slots=n.value, slot_bytes=b.value, running=r.value, waiting=w.value, h_pages=hp.value,
+                    h_page_bytes=hb.value, r_pages=rp.value, r_page_bytes=rb.value, peak_running=pk.value,
+                    device_bytes=n.value * b.value + hp.value * hb.value + rp.value * rb.value)
 
     def submit(self, q, tag: int):
         keep = []

@@ -69,6 +69,7 @@ void destroy_slot(Slot* s) {
   for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_ctl) cudaFreeHost(s->h_ctl);            // h_res lies inside it
+  if (s->lrec) cudaFree(s->lrec);
   if (s->st) cudaStreamDestroy(s->st);
   delete s;
 }
@@ -89,61 +90,91 @@ static uint32_t target_min_work() {
   return uint32_t(v);
 }
 
-int create_slot(rpq_kg* kg, Slot** out) {
-  Slot* s = new Slot();
+// Device arrays of one slot: (destination, bytes) in allocation order.  With
+// own_cols the slot holds all kMaxCols hit-level and recovery columns; a
+// server slot holds none (its queries borrow column pages).
+// Visited bytes and the three bit maps share one allocation (cleared per run
+// by one memset): bytes of the visited part and of each bit map.
+static void run_clear_layout(size_t n, size_t* vb, size_t* fb) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  *vb = up(((n + 3) / 4) * 4 + 16);
+  *fb = up((n + 31) / 32 * 4 + 16);
+}
+
+static std::vector<std::pair<void**, size_t>> slot_arrays(const rpq_kg* kg, DevSlot& d, bool own_cols) {
   const size_t n = size_t(kg->dev.n);
-  const size_t nwords = (n + 31) / 32;
-  DevSlot& d = s->d;
   d.cap = uint32_t(std::max<size_t>(n, 1));
-  auto A = [&](void** p, size_t bytes) -> int {
-    const int rc = alloc_device(p, bytes, &s->bytes);
-    if (rc == RPQ_OK) s->allocs.push_back(*p);
-    return rc;
-  };
-  int rc = RPQ_OK;
-#define SA(ptr, bytes) do { if (rc == RPQ_OK) rc = A((void**)&(ptr), (bytes)); } while (0)
   d.hp = uint32_t((n + 15) / 16 * 16);
-  SA(d.H, size_t(d.hp) * kMaxCols + 16);
-  {   // per-run state cleared by one memset: visited bytes, F[0], F[1], cf
-    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t vb = up(((n + 3) / 4) * 4 + 16), fb = up(nwords * 4 + 16);
-    d.run_clear_bytes = vb + 3 * fb;
-    SA(d.run_clear, d.run_clear_bytes);
-    if (rc == RPQ_OK) {
-      char* b = static_cast<char*>(d.run_clear);
-      d.vis = reinterpret_cast<uint32_t*>(b);
-      d.F[0] = reinterpret_cast<uint32_t*>(b + vb);
-      d.F[1] = reinterpret_cast<uint32_t*>(b + vb + fb);
-      d.cf = reinterpret_cast<uint32_t*>(b + vb + 2 * fb);
-    }
-  }
-  SA(d.stopl, n + 16);
-  SA(d.items, sizeof(Item) * d.cap);
-  SA(d.imask, sizeof(uint16_t) * d.cap + 16);
-  SA(d.cg, sizeof(uint32_t) * d.cap);
-  SA(d.topk, sizeof(uint32_t) * size_t(num_sms()) * 2 * kMaxK);   // k_topk runs 2 blocks per SM
-  SA(d.rmask, sizeof(unsigned long long) * d.cap * kMaxCols);
-  SA(d.vmask, sizeof(unsigned long long) * d.cap);
-  SA(d.rlist, sizeof(uint32_t) * d.cap * kMaxCols);
-  SA(d.rcnt, sizeof(uint32_t) * kRecStride * kMaxCols);
   d.tile_cap = uint32_t(uint64_t(kg->m2) / 128 + 2);
-  SA(d.tile_first, sizeof(uint32_t) * d.tile_cap);
-  SA(d.fq[0], sizeof(uint32_t) * d.cap);         // any queue limit up to n fits
-  SA(d.fq[1], sizeof(uint32_t) * d.cap);
-  SA(d.ulist, sizeof(uint32_t) * d.cap);
-  SA(d.vcl, sizeof(uint32_t) * d.cap);
   d.tgt_cap = d.cap;
-  SA(d.tgt, sizeof(uint32_t) * d.tgt_cap);
-  SA(d.sticky, 16);
-  SA(d.ctl, kCtlBytes + sizeof(rpq_result) * kMaxK);   // the results follow the control block:
-  if (rc == RPQ_OK) d.res = reinterpret_cast<char*>(d.ctl) + kCtlBytes;   // one copy returns both
-  SA(d.q, sizeof(QueryDev));
-  SA(d.n_res, 16);
-  SA(d.bar, 16);
-#undef SA
+  size_t vb = 0, fb = 0;
+  run_clear_layout(n, &vb, &fb);
+  d.run_clear_bytes = vb + 3 * fb;             // visited bytes, F[0], F[1], cf
+  std::vector<std::pair<void**, size_t>> v = {
+      {&d.run_clear, d.run_clear_bytes},
+      {(void**)&d.stopl, n + 16},
+      {(void**)&d.items, sizeof(Item) * d.cap},
+      {(void**)&d.imask, sizeof(uint16_t) * d.cap + 16},
+      {(void**)&d.cg, sizeof(uint32_t) * d.cap},
+      {(void**)&d.topk, sizeof(uint32_t) * size_t(num_sms()) * 2 * kMaxK},   // k_topk: 2 blocks per SM
+      {(void**)&d.vmask, sizeof(unsigned long long) * d.cap},
+      {(void**)&d.rcnt, sizeof(uint32_t) * kRecStride * kMaxCols},
+      {(void**)&d.tile_first, sizeof(uint32_t) * d.tile_cap},
+      {(void**)&d.fq[0], sizeof(uint32_t) * d.cap},       // any queue limit up to n fits
+      {(void**)&d.fq[1], sizeof(uint32_t) * d.cap},
+      {(void**)&d.ulist, sizeof(uint32_t) * d.cap},
+      {(void**)&d.vcl, sizeof(uint32_t) * d.cap},
+      {(void**)&d.tgt, sizeof(uint32_t) * d.tgt_cap},
+      {(void**)&d.sticky, 16},
+      {(void**)&d.ctl, kCtlBytes + sizeof(rpq_result) * kMaxK},   // the results follow the control block
+      {(void**)&d.q, sizeof(QueryDev)},
+      {(void**)&d.n_res, 16},
+      {(void**)&d.bar, 16},
+  };
+  if (own_cols) {
+    v.push_back({(void**)&d.H, size_t(d.hp) * kMaxCols + 16});
+    v.push_back({(void**)&d.rmask, sizeof(unsigned long long) * d.cap * kMaxCols});
+    v.push_back({(void**)&d.rlist, sizeof(uint32_t) * d.cap * kMaxCols});
+  }
+  return v;
+}
+
+int64_t slot_bytes(const rpq_kg* kg, bool own_cols) {
+  DevSlot d{};
+  int64_t t = 0;
+  for (const auto& a : slot_arrays(kg, d, own_cols)) t += int64_t(a.second);
+  return t;
+}
+
+// Clock cycles a block of the persistent kernel waits at a grid barrier
+// before it reports RPQ_ETIMEOUT: about 1 s at 2 GHz, or RPQ_BARRIER_LIMIT
+// (cycles, at least 1), which the timeout test sets small.
+static long long barrier_limit() {
+  static long long v = -1;
+  if (v < 0) { const char* e = getenv("RPQ_BARRIER_LIMIT"); v = (e && *e) ? std::max(1LL, atoll(e)) : 2000000000LL; }
+  return v;
+}
+
+int create_slot(rpq_kg* kg, Slot** out, bool own_cols) {
+  Slot* s = new Slot();
+  DevSlot& d = s->d;
+  int rc = RPQ_OK;
+  for (const auto& a : slot_arrays(kg, d, own_cols)) {
+    rc = alloc_device(a.first, a.second, &s->bytes);
+    if (rc != RPQ_OK) break;
+    s->allocs.push_back(*a.first);
+  }
   if (rc == RPQ_OK) {
+    char* b = static_cast<char*>(d.run_clear);
+    size_t vb = 0, fb = 0;
+    run_clear_layout(size_t(kg->dev.n), &vb, &fb);
+    d.vis = reinterpret_cast<uint32_t*>(b);
+    d.F[0] = reinterpret_cast<uint32_t*>(b + vb);
+    d.F[1] = reinterpret_cast<uint32_t*>(b + vb + fb);
+    d.cf = reinterpret_cast<uint32_t*>(b + vb + 2 * fb);
+    d.res = reinterpret_cast<char*>(d.ctl) + kCtlBytes;   // one copy returns control block and results
     // masks start at zero; the recovery kernel restores zero after each use
-    if (cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess ||
+    if ((own_cols && cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess) ||
         cudaMemset(d.vmask, 0, sizeof(unsigned long long) * d.cap) != cudaSuccess ||
         cudaMemset(d.rcnt, 0, sizeof(uint32_t) * kRecStride * kMaxCols) != cudaSuccess ||
         cudaMemset(d.sticky, 0, 16) != cudaSuccess ||
@@ -161,6 +192,7 @@ int create_slot(rpq_kg* kg, Slot** out) {
   d.qcap = 0;
   d.target = use_target() ? 1u : 0u;
   d.tgt_min_work = target_min_work();
+  d.bar_limit = barrier_limit();
   apply_tuning(kg, s);
   *out = s;
   return RPQ_OK;
@@ -177,6 +209,7 @@ static bool persistent_slot0() {
   if (v < 0) { const char* e = getenv("RPQ_PERSISTENT"); v = (e && *e == '1') ? 1 : 0; }
   return v == 1;
 }
+
 
 int get_slot(rpq_kg* kg, size_t i, Slot** out) {
   while (kg->slots.size() <= i) {
@@ -311,9 +344,18 @@ static int build_query_graph(rpq_kg* kg, Slot* s, int n_m, int L, int K, cudaGra
 // Enqueue the body of a query: replay (or build, then replay) the graph of
 // its shape, or launch the kernels directly.
 static int enqueue_body(rpq_kg* kg, Slot* s, int n_c, int n_m, int L) {
-  if (!use_graphs() || kg->prof) {
+  if (kg->prof) {                                       // direct launches with per-level records
     RPQ_CUDA(cudaGetLastError());
-    return launch_query_body(kg->dev, s->d, n_m, L, s->st, kg->prof, true);
+    const size_t rb = sizeof(LevelRec) * 2 * kLogLevels;
+    if (!s->lrec) RPQ_CUDA(cudaMalloc((void**)&s->lrec, rb));
+    RPQ_CUDA(cudaMemsetAsync(s->lrec, 0, rb, s->st));
+    DevSlot d = s->d;
+    d.lrec = s->lrec;
+    return launch_query_body(kg->dev, d, n_m, L, s->st, kg->prof, true);
+  }
+  if (!use_graphs()) {
+    RPQ_CUDA(cudaGetLastError());
+    return launch_query_body(kg->dev, s->d, n_m, L, s->st, nullptr, true);
   }
   (void)n_c;
   const int K = s->d.persistent ? L + 1 : flat_levels(kg, L);
@@ -355,6 +397,7 @@ int start_query(rpq_kg* kg, Slot* s, const QueryDev& qv) {
                            cudaMemcpyDeviceToHost, s->st));      // control block and results
   s->busy = true;
   s->pending_k = qv.k;
+  s->pending_nc = qv.n_c;
   s->pending_nm = qv.n_m;
   return RPQ_OK;
 }
@@ -375,11 +418,48 @@ void fill_stats(const Ctl& c, rpq_stats* st) {
   st->e_act_skipped = int64_t(c.e_act_skip);
 }
 
+// Profiling mode: pair the level kernels' device times of the slot's
+// finished query with its per-level records (the query's launches are
+// complete once the slot's stream has been synchronised).
+static int collect_level_profile(rpq_kg* kg, Slot* s) {
+  Prof* pf = kg->prof;
+  pf->collect(s->st);
+  if (!s->lrec) return RPQ_OK;
+  std::vector<LevelRec> rec(2 * kLogLevels);
+  RPQ_CUDA(cudaMemcpy(rec.data(), s->lrec, sizeof(LevelRec) * rec.size(), cudaMemcpyDeviceToHost));
+  size_t keep = 0;
+  for (const Prof::LevelTimes& lt : pf->level_times) {
+    if (lt.st != s->st) { pf->level_times[keep++] = lt; continue; }
+    const LevelRec& r = rec[size_t(lt.run) * kLogLevels + size_t(lt.level)];
+    if (!r.flags) continue;                         // a launch after the run had stopped
+    rpq_level_profile p;
+    memset(&p, 0, sizeof(p));
+    p.run = lt.run;
+    p.level = lt.level;
+    p.flags = int32_t(r.flags);
+    p.frontier = int32_t(r.frontier);
+    p.columns = lt.run == 0 ? s->pending_nc : s->pending_nm;
+    p.units = int64_t(r.units);
+    p.items = int64_t(r.items);
+    p.e_act = int64_t(r.eact);
+    p.claims = int64_t(r.claims);
+    p.enqueue_ms = lt.ms[kKindEnqueue];
+    p.target_ms = lt.ms[kKindTarget];
+    p.expand_ms = lt.ms[kKindExpand];
+    pf->levels.push_back(p);
+  }
+  pf->level_times.resize(keep);
+  return RPQ_OK;
+}
+
 // Wait for the slot's query and copy its results out.
 int finish_query(rpq_kg* kg, Slot* s, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
   s->busy = false;
   RPQ_CUDA(cudaStreamSynchronize(s->st));
-  if (kg->prof) kg->prof->collect();
+  if (kg->prof) {
+    const int prc = collect_level_profile(kg, s);
+    if (prc != RPQ_OK) return prc;
+  }
   const Ctl& c = *s->h_ctl;
   const int rc = dev_err_to_status(c.err);
   if (rc != RPQ_OK) return rc;
@@ -810,6 +890,18 @@ int rpq_profile_read(rpq_kg* kg, rpq_profile* out, int32_t reset) {
   if (reset) {
     for (int i = 0; i < RPQ_PROF_CLASSES; ++i) { kg->prof->ms[i] = 0; kg->prof->launches[i] = 0; }
   }
+  return RPQ_OK;
+}
+
+int rpq_profile_levels(rpq_kg* kg, rpq_level_profile* out, int32_t cap, int32_t* n_out, int32_t reset) {
+  if (!kg || !n_out || cap < 0 || (cap > 0 && !out)) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
+  *n_out = 0;
+  if (!kg->prof) return RPQ_OK;
+  const std::vector<rpq_level_profile>& v = kg->prof->levels;
+  const size_t n = std::min(v.size(), size_t(cap));
+  if (n) memcpy(out, v.data(), sizeof(rpq_level_profile) * n);
+  *n_out = int32_t(v.size());
+  if (reset) kg->prof->levels.clear();
   return RPQ_OK;
 }
 

@@ -29,6 +29,7 @@ int alloc_device(void** p, size_t bytes, int64_t* counter);
 // staging for results and the graphs captured for each query shape.
 struct Slot {
   DevSlot d{};
+  LevelRec* lrec = nullptr;      // per-level records of the current query (profiling mode)
   cudaStream_t st = nullptr;
   int64_t bytes = 0;
   Ctl* h_ctl = nullptr;
@@ -37,33 +38,58 @@ struct Slot {
   std::unordered_map<uint64_t, cudaGraphExec_t> graphs;
   bool busy = false;
   int32_t pending_k = 0;
+  int32_t pending_nc = 0;
   int32_t pending_nm = 0;
 };
 
 // Optional per-launch timing with CUDA events (profiling mode, no graphs).
 struct SgScratch;   // subgraph.cu
 
+// Launch kinds of the level kernels in a Glevel record (profiling).
+enum LaunchKind { kKindOther = 0, kKindEnqueue, kKindTarget, kKindExpand };
+
 struct Prof {
-  struct Rec { int cls; cudaEvent_t a, b; };
+  struct Rec { int cls; cudaEvent_t a, b; cudaStream_t st; int run, level, kind; };
+  // Device times of the level kernels of one Glevel of one run of a query.
+  struct LevelTimes { cudaStream_t st; int run, level; double ms[4]; };
   std::vector<cudaEvent_t> pool;
   std::vector<Rec> pending;
+  std::vector<LevelTimes> level_times;   // per Glevel, in launch order, until paired with its record
+  std::vector<rpq_level_profile> levels; // finished Glevel profiles (rpq_profile_levels)
   double ms[RPQ_PROF_CLASSES] = {};
   int64_t launches[RPQ_PROF_CLASSES] = {};
+  int tag_run = -1, tag_level = -1, tag_kind = kKindOther;   // set by the launcher before a level kernel
   cudaEvent_t take() {
     if (pool.empty()) { cudaEvent_t e; cudaEventCreate(&e); return e; }
     cudaEvent_t e = pool.back(); pool.pop_back(); return e;
   }
   void begin(cudaStream_t st, cudaEvent_t* a) { *a = take(); cudaEventRecord(*a, st); }
   void end(int cls, cudaStream_t st, cudaEvent_t a) {
-    cudaEvent_t b = take(); cudaEventRecord(b, st); pending.push_back({cls, a, b});
+    cudaEvent_t b = take(); cudaEventRecord(b, st);
+    pending.push_back({cls, a, b, st, tag_run, tag_level, tag_kind});
+    tag_kind = kKindOther;
   }
-  void collect() {  // after the stream has been synchronised
+  // Timings of the launches of stream `st` (after it has been synchronised;
+  // every stream when st is NULL).
+  void collect(cudaStream_t st = nullptr) {
+    size_t keep = 0;
     for (const Rec& r : pending) {
+      if (st && r.st != st) { pending[keep++] = r; continue; }
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) { ms[r.cls] += t; launches[r.cls] += 1; }
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+        if (r.kind != kKindOther && r.level >= 0) {
+          LevelTimes* lt = nullptr;
+          for (auto it = level_times.rbegin(); it != level_times.rend(); ++it)
+            if (it->st == r.st && it->run == r.run && it->level == r.level) { lt = &*it; break; }
+          if (!lt) { level_times.push_back({r.st, r.run, r.level, {0, 0, 0, 0}}); lt = &level_times.back(); }
+          lt->ms[r.kind] += t;
+        }
+      }
       pool.push_back(r.a); pool.push_back(r.b);
     }
-    pending.clear();
+    pending.resize(keep);
   }
   ~Prof() { for (cudaEvent_t e : pool) cudaEventDestroy(e); }
 };
@@ -96,7 +122,8 @@ namespace rpq {
 int build_graph(rpq_kg* kg, const rpq_kg_desc* d);
 
 // Search slots and query execution (api.cu).
-int create_slot(rpq_kg* kg, Slot** out);
+int create_slot(rpq_kg* kg, Slot** out, bool own_cols = true);
+int64_t slot_bytes(const rpq_kg* kg, bool own_cols);   // device bytes create_slot allocates
 void destroy_slot(Slot* s);
 int get_slot(rpq_kg* kg, size_t i, Slot** out);
 int check_query(const rpq_kg* kg, const rpq_query* q, QueryDev* qv, bool* empty);

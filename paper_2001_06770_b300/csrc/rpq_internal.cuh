@@ -77,12 +77,20 @@ struct __align__(8) Item {
 };
 
 // Query parameters as the kernels read them (device copy in the slot).
+// The query's keyword columns live where the host placed them: column j of
+// the Node-Keyword Matrix at hc[j] (one byte per node), and the recovery's
+// CG masks and node list of central column j at rm[j] and rl[j] (cap
+// entries each).  A slot that owns its columns points them at its own
+// arrays; a server lends each query pages for just its |T| columns.
 struct QueryDev {
   int32_t kw[2 * kMaxCols];  // central ids then marginal ids
   int32_t n_c, n_m, k, L;
   double gamma;
   int32_t w;                 // CG beam width, k <= w <= kMaxK
   int32_t product;           // multiplicative S^r = S^c * S^m
+  uint8_t* hc[kMaxCols];
+  unsigned long long* rm[kMaxCols];
+  uint32_t* rl[kMaxCols];
 };
 
 // Control block of one slot, read and updated by the kernels of a search.
@@ -116,7 +124,8 @@ struct Ctl {
   uint32_t topk_done;          // k_topk: blocks finished
   uint32_t rec_done;           // recovery: CTAs finished
   unsigned long long e_act[2];  // per run
-  unsigned long long hits[2];
+  unsigned long long hits[2];   // first hits, counted when the run stops
+  unsigned long long seeded[2]; // (node, column) pairs seeded with h = 0
   unsigned long long units, items, frontier;  // work totals of both runs
   int32_t levels[2];           // last identified level per run
   int32_t sel[kMaxK];
@@ -125,12 +134,30 @@ struct Ctl {
   uint8_t sm[kMaxK];
 };
 
+// Per-Glevel record of one query, kept while kernels are profiled: the level
+// kernels of Glevel l of run r write entry r * kLogLevels + l.
+constexpr int kLogLevels = kMaxLevel + 1;
+enum LevelFlags : uint32_t {
+  kLvlExpanded = 1u,   // the expansion ran
+  kLvlSkipped = 2u,    // the V_C check skipped the expansion
+  kLvlStop = 4u,       // the run stopped at this level
+  kLvlQueue = 8u,      // the enqueue read the frontier queue (else the bit map)
+};
+struct LevelRec {
+  unsigned long long units;    // work units (CSR entries of the items' segments)
+  unsigned long long items;    // expansion items
+  unsigned long long eact;     // (column, edge) activations the expansion executed
+  unsigned long long claims;   // (node, column) claims written (h = l+1)
+  uint32_t frontier;           // |Q_l|
+  uint32_t flags;              // LevelFlags
+};
+
 // Bytes of the control block in a slot's control allocation; the results
 // (rpq_result[kMaxK]) follow it there, so one copy returns both.
 constexpr size_t kCtlBytes = (sizeof(Ctl) + 15) / 16 * 16;
 
 struct DevSlot {
-  uint8_t* H;
+  uint8_t* H;                 // the slot's own columns (kMaxCols * hp bytes), or NULL (server slots)
   uint32_t* vis;
   uint32_t* F[2];
   uint32_t* cf;
@@ -139,9 +166,9 @@ struct DevSlot {
   uint16_t* imask;            // column masks of the items
   uint32_t* cg;
   uint32_t* topk;             // k_topk: survivors of each block (w per block)
-  unsigned long long* rmask;  // recovery: per-column CG mask per node (kMaxCols * cap)
+  unsigned long long* rmask;  // recovery: the slot's own per-column CG masks (kMaxCols * cap), or NULL
   unsigned long long* vmask;  // recovery: union over columns
-  uint32_t* rlist;            // recovery: per-column node lists (kMaxCols * cap)
+  uint32_t* rlist;            // recovery: the slot's own per-column node lists (kMaxCols * cap), or NULL
   uint32_t* rcnt;             // recovery: per-column counters (kMaxCols * kRecStride), zero between uses
   uint32_t* tile_first;       // expansion: first item of each warp tile
   uint32_t tile_cap;
@@ -163,6 +190,8 @@ struct DevSlot {
   uint32_t* sticky;           // device error bits kept across queries
   unsigned* bar;              // grid barrier of the persistent run kernel: count, generation
   uint32_t persistent;        // run each level loop as one cooperative k_run launch
+  long long bar_limit;        // clock cycles a block waits at a grid barrier before it gives up
+  LevelRec* lrec;             // per-level records (2 * kLogLevels) while profiling, else NULL
   Ctl* ctl;
   QueryDev* q;
   void* res;                  // rpq_result[kMaxK] on the device
@@ -170,6 +199,18 @@ struct DevSlot {
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Column pointers of the current query.  They do not change while the
+// query's kernels run, so they are read through the read-only path.
+__device__ __forceinline__ uint8_t* hcol(const QueryDev& q, int j) {
+  return reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.hc[j])));
+}
+__device__ __forceinline__ unsigned long long* rmcol(const QueryDev& q, int j) {
+  return reinterpret_cast<unsigned long long*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.rm[j])));
+}
+__device__ __forceinline__ uint32_t* rlcol(const QueryDev& q, int j) {
+  return reinterpret_cast<uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.rl[j])));
+}
 
 __device__ __forceinline__ uint8_t vis_byte(const uint32_t* vis, uint32_t v) {
   return reinterpret_cast<const uint8_t*>(vis)[v];

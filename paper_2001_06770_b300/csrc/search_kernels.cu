@@ -30,9 +30,12 @@
 // a, so they form one segment).  An edge with a smaller max was already
 // handled at that earlier level by the same node (which was in the frontier
 // then, because it is retained while it has an edge with a > level), so
-// skipping Algorithm 1's re-scan changes no h value.  Writes of h store the
-// same value l+1 whoever wins (Theorem 6); the atomicOr on the visited byte
-// only decides which thread performs the single write.
+// skipping Algorithm 1's re-scan changes no h value.  Every thread that finds
+// a column of a neighbour unreached (its visited bit clear) at level l writes
+// h = l+1 there: the visited bits set before the launch are all visible, so
+// the column was not reached at an earlier level, and any other writer of
+// this launch stores the same l+1 (Theorem 6).  The visited and frontier
+// bits are then set with reductions that return nothing.
 #include <algorithm>
 #include <cstdio>
 
@@ -164,6 +167,7 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
     len[j] = g.kw_ptr[kw + 1] - beg[j];
     total += len[j];
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->seeded[run] = total;   // (node, column) pairs with h = 0
   uint32_t* F0 = s.F[0];
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t end = (total + 31u) & ~31u;            // whole warps for the queue push
@@ -177,7 +181,7 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
       const int32_t vv = g.kw_nodes[beg[j] + r];
       if (vv >= 0 && vv < g.n) {
         v = uint32_t(vv);
-        s.H[size_t(j) * s.hp + v] = 0;
+        hcol(q, j)[v] = 0;
         vis_or(s.vis, v, 1u << j);
         const uint32_t old = atomicOr(F0 + (v >> 5), 1u << (v & 31));
         fresh = !((old >> (v & 31)) & 1u);
@@ -297,7 +301,10 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   // level is usually followed by a dense one, and its appends would all
   // contend on one counter).  Every block computes the same `sparse` from
   // values no kernel changes during this level; k_expand reads fq_use.
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->fq_use[p ^ 1] = sparse ? 1u : 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->fq_use[p ^ 1] = sparse ? 1u : 0u;
+    if (s.lrec && sparse) s.lrec[run * kLogLevels + l].flags |= kLvlQueue;
+  }
   const uint32_t nwords = (uint32_t(g.n) + 31u) >> 5;
   const uint32_t nsrc = sparse ? fq_n : nwords * 32u;   // candidate slots
   // slots per block tile: one round per thread for the queue (short frontiers
@@ -357,7 +364,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         rb = g.row_ptr[v];
         re = g.row_ptr[v + 1];
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? ldx<P>(s.H + size_t(j) * s.hp + v) : 0u;
+        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? ldx<P>(hcol(q, j) + v) : 0u;
         if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
         if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
       }
@@ -529,7 +536,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
       if (e < hi) {
         const uint32_t x = __ldg(g.adj + e);
         const uint32_t a = x >> kNodeBits, u = x & kNodeMask;
-        const uint32_t vb = vis_byte(s.vis, u), hu = s.H[size_t(j) * s.hp + u];
+        const uint32_t vb = vis_byte(s.vis, u), hu = hcol(q, int(j))[u];
         const uint32_t cfw = s.cf[u >> 5], stl = s.stopl[u];
         if ((vb >> j) & 1u) {
           const uint32_t lam = a > hu ? a : hu;
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
   uint32_t hits = 0;
   for (uint32_t i = threadIdx.x; !over && i < nf; i += blockDim.x) {
     const uint32_t x = __ldcg(s.tgt + i), j = x >> kNodeBits, v = x & kNodeMask;
-    s.H[size_t(j) * s.hp + v] = uint8_t(l + 1);         // a repeated (node, column) writes the same value
+    hcol(q, int(j))[v] = uint8_t(l + 1);                 // a repeated (node, column) writes the same value
     const uint32_t old = atomicOr(s.vis + (v >> 2), (1u << j) << ((v & 3u) * 8u));
     if ((old >> ((v & 3u) * 8u + j)) & 1u) continue;
     ++hits;
@@ -593,7 +600,6 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
     const bool stop_next = l + 1 >= uint32_t(q.L) || cnt >= nsel ||
                            (cnt >= uint32_t(q.k) && theorem4_stop(c, s_matched, s_sm, q, nsel, l + 1));
     if (!over && s_hits && stop_next) c->skip_lvl = l + 1;
-    if (s_hits) atomicAdd(&c->hits[1], (unsigned long long)s_hits);
     c->tgt_n = 0;
     c->tgt_done = 0;
   }
@@ -624,6 +630,26 @@ __device__ __forceinline__ void load_window(const Item* items, const uint16_t* i
   }
 }
 
+// First hits of a finished run: the (node, column) pairs its visited bits
+// hold, less the seeds (h = 0).  Every block of the stopping launch takes a
+// share of the visited words; the expansions themselves count no hits.
+template <bool P>
+__device__ void count_hits(const DevKG& g, const DevSlot& s, int run, uint64_t* s_warp) {
+  Ctl* c = s.ctl;
+  const int nt = run == 0 ? s.q->n_c : s.q->n_m;
+  const uint32_t colmask = ((1u << nt) - 1u) * 0x01010101u;      // the run's columns in each byte
+  const uint32_t nwords = (uint32_t(g.n) + 3u) >> 2;
+  uint64_t cnt = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
+    cnt += __popc(ldx<P>(s.vis + i) & colmask);
+  const uint64_t tot = block_sum(cnt, s_warp);
+  if (threadIdx.x == 0) {
+    unsigned long long add = tot;
+    if (blockIdx.x == 0) add -= ldx<P>(&c->seeded[run]);        // modulo 2^64: the sum comes out right
+    if (add) atomicAdd(&c->hits[run], add);
+  }
+}
+
 // Returns true when the run stops at level l (no expansion then).
 template <bool P>
 __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, int run, uint32_t l,
@@ -645,6 +671,15 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
     c->frontier += nq;
     const unsigned long long ea = ldx<P>(&c->eact_lvl[p]);   // enqueued activations of this level
     c->eact_lvl[p] = 0;
+    if (s.lrec) {                                  // profiling: the level's work
+      LevelRec& lr = s.lrec[run * kLogLevels + l];
+      const bool ran = !stop && !skip;
+      lr.frontier = nq;
+      lr.units = ran ? n_work : 0;
+      lr.items = ran ? n_items : 0;
+      lr.eact = ran ? ea : 0;
+      lr.flags |= stop ? kLvlStop : (skip ? kLvlSkipped : kLvlExpanded);
+    }
     if (stop) {
       c->done = 1;
       c->levels[run] = (nq == 0 && l > 0) ? int32_t(l) - 1 : int32_t(l);
@@ -667,10 +702,11 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       c->fq_over[p] = 0;
     }
   }
+  __shared__ uint64_t s_warp[33];
+  if (stop) count_hits<P>(g, s, run, s_warp);
   if (stop && run == 1 && blockIdx.x == 0) write_results(s);   // the marginal run ends here
   if (stop || skip || n_work == 0) return stop;
 
-  __shared__ uint64_t s_warp[33];
   uint32_t* Fn = s.F[p ^ 1];
   // The next level's queue (started by k_enqueue of this level) is kept only
   // if this level's work is small; a large level would overflow it anyway and
@@ -682,7 +718,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t ntiles = (n_work + kWarpTile - 1) / kWarpTile;
-  uint64_t hits = 0, completed = 0;                  // completed: nodes that now hold every central column
+  uint64_t claims = 0, completed = 0;                // completed: nodes that now hold every central column
   const uint32_t fullc = run == 0 ? (1u << q.n_c) - 1u : 0x100u;
   for (uint32_t t = gw; t < ntiles; t += nwarps) {
     const uint32_t t0 = t * kWarpTile;
@@ -720,7 +756,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
     // candidate new columns of every round, then all atomics in flight together
-    uint32_t nw_r[kExpRounds], old_r[kExpRounds];
+    uint32_t nw_r[kExpRounds];
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) {
       nw_r[r] = 0;
@@ -730,35 +766,42 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
       nw_r[r] = act & ~vb_r[r];
     }
-#pragma unroll
-    for (int r = 0; r < kExpRounds; ++r) {
-      const uint32_t nb = x_r[r] & kNodeMask;
-      old_r[r] = nw_r[r] ? atomicOr(s.vis + (nb >> 2), nw_r[r] << ((nb & 3u) * 8u)) : 0u;
-    }
+    // Claims: h = l+1 for every column found unreached, then the visited and
+    // frontier bits by reductions.  A returning atomic only where its old
+    // value is used: when this claim may complete a central node (the count
+    // lets the next enqueue skip its work items if the run stops there; a
+    // completion whose claims all looked incomplete is not counted, which
+    // only forgoes that saving), and for the frontier bit while the next
+    // level's queue is filled (a node is queued once).
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) {
       bool fresh = false;
       const uint32_t nb = x_r[r] & kNodeMask;
-      const uint32_t won = nw_r[r] & ~(old_r[r] >> ((nb & 3u) * 8u)) & 0xffu;
-      if (won) {
-        for (uint32_t m = won; m; m &= m - 1) s.H[size_t(__ffs(m) - 1) * s.hp + nb] = uint8_t(l + 1);
-        if (use_next) {                              // the old word is needed only to fill the queue
+      const uint32_t nw = nw_r[r];
+      if (nw) {
+        for (uint32_t m = nw; m; m &= m - 1) hcol(q, __ffs(m) - 1)[nb] = uint8_t(l + 1);
+        const uint32_t sh = (nb & 3u) * 8u;
+        if (((vb_r[r] | nw) & fullc) == fullc) {
+          const uint32_t ob = (atomicOr(s.vis + (nb >> 2), nw << sh) >> sh) & 0xffu;
+          completed += (ob & fullc) != fullc && ((ob | nw) & fullc) == fullc;   // one claim completes the node
+        } else {
+          atomicOr(s.vis + (nb >> 2), nw << sh);       // result unused: a reduction
+        }
+        if (use_next) {
           const uint32_t of = atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
           fresh = !((of >> (nb & 31u)) & 1u);
         } else {
           atomicOr(Fn + (nb >> 5), 1u << (nb & 31u));
         }
-        hits += __popc(won);
-        const uint32_t ob = (old_r[r] >> ((nb & 3u) * 8u)) & 0xffu;
-        completed += ((ob | won) & fullc) == fullc;     // exactly one writer completes a node
+        claims += __popc(nw);
       }
       queue_push(s, c, p ^ 1, use_next, fresh, nb);
     }
   }
-  const uint64_t hc = block_sum(hits | (completed << 40), s_warp);   // both counts in one reduction
-  const uint64_t th = hc & ((1ull << 40) - 1ull), tc = hc >> 40;
-  if (threadIdx.x == 0 && th) atomicAdd(&c->hits[run], (unsigned long long)th);
+  const uint64_t cc = block_sum(claims | (completed << 40), s_warp);   // both counts in one reduction
+  const uint64_t tcl = cc & ((1ull << 40) - 1ull), tc = cc >> 40;
   if (threadIdx.x == 0 && tc) atomicAdd(&c->cg_next[p ^ 1], uint32_t(tc));
+  if (threadIdx.x == 0 && tcl && s.lrec) atomicAdd(&s.lrec[run * kLogLevels + l].claims, (unsigned long long)tcl);
   return false;
 }
 
@@ -777,11 +820,10 @@ k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_gr
 // All Glevels of one run in one cooperative launch (every block resident):
 // the enqueue and expansion phases of a level are separated by a grid
 // barrier instead of a kernel boundary.  The barrier is bounded: a block that
-// waits longer than kBarrierCycles sets kErrTimeout and every block leaves
-// the kernel at its next barrier, so the kernel always ends.
-constexpr long long kBarrierCycles = 2000000000ll;   // ~1 s at 2 GHz
-
-__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, uint32_t* err) {
+// waits longer than the slot's bar_limit clock cycles (about 1 s by default)
+// sets kErrTimeout and every block leaves the kernel at its next barrier, so
+// the kernel always ends.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, uint32_t* err, long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -796,7 +838,7 @@ __device__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, u
       const long long t0 = clock64();
       while (*(volatile unsigned*)gen == g0) {
         if (*(volatile uint32_t*)err & kErrTimeout) { ok = 0; break; }
-        if (clock64() - t0 > kBarrierCycles) { atomicOr(err, kErrTimeout); ok = 0; break; }
+        if (clock64() - t0 > limit) { atomicOr(err, kErrTimeout); ok = 0; break; }
         __nanosleep(32);
       }
     }
@@ -814,9 +856,9 @@ k_run(DevKG g, DevSlot s, int run) {
     const uint32_t l = *(volatile uint32_t*)&c->lvl_enq;
     if (blockIdx.x == 0 && threadIdx.x == 0) { c->lvl_exp = l; c->iters[run] += 1; }
     enqueue_level<true>(g, s, run, l);
-    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) break;
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
     if (expand_level<true>(g, s, run, l, 0, 0)) return;
-    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err)) break;
+    if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
   }
   // a barrier ran out: the run ends without results; the error reaches the
   // slot's sticky word (read by rpq_sync_device) as well as the control block
@@ -1026,7 +1068,7 @@ __device__ __forceinline__ bool holds_central(const DevSlot& s, const QueryDev& 
   const uint32_t vb = vis_byte(s.vis, v);
   uint32_t h[kMaxCols];
 #pragma unroll
-  for (int jj = 0; jj < kMaxCols; ++jj) h[jj] = jj < q.n_c ? s.H[size_t(jj) * s.hp + v] : 1u;
+  for (int jj = 0; jj < kMaxCols; ++jj) h[jj] = jj < q.n_c ? hcol(q, jj)[v] : 1u;
   bool holds = false;
 #pragma unroll
   for (int jj = 0; jj < kMaxCols; ++jj) holds |= ((vb >> jj) & 1u) && h[jj] == 0;
@@ -1044,9 +1086,9 @@ k_recover_cols(DevKG g, DevSlot s) {
   if (nsel == 0 || j >= q.n_c) return;                     // the same in every CTA of the cluster
   const int maxlev = c->levels[0];
   const uint32_t cap = s.cap;
-  const uint8_t* Hj = s.H + size_t(j) * s.hp;
-  unsigned long long* rmask = s.rmask + size_t(j) * cap;
-  uint32_t* rlist = s.rlist + size_t(j) * cap;
+  const uint8_t* Hj = hcol(q, j);
+  unsigned long long* rmask = rmcol(q, j);
+  uint32_t* rlist = rlcol(q, j);
   uint32_t* sn = s.rcnt + size_t(j) * kRecStride;          // sn[y]: segment length of level y
   uint32_t* ovf = sn + (kMaxLevel + 2);                    // overflow length
   __shared__ uint32_t s_off[kRecThreads];
@@ -1250,7 +1292,19 @@ static void timed(Prof* prof, int cls, cudaStream_t st, F&& launch) {
 }
 
 int launch_query_setup(const DevSlot& s, const QueryDev& qv, const int32_t* d_kw, cudaStream_t st) {
-  k_set_query<<<1, 32, 0, st>>>(s, qv, d_kw);
+  QueryDev q = qv;
+  if (s.H) {                                  // the slot's own columns
+    for (int j = 0; j < kMaxCols; ++j) {
+      q.hc[j] = s.H + size_t(j) * s.hp;
+      q.rm[j] = s.rmask + size_t(j) * s.cap;
+      q.rl[j] = s.rlist + size_t(j) * s.cap;
+    }
+  } else {                                    // columns lent by a server: every used one is set
+    const int nh = std::max(q.n_c, q.n_m);
+    for (int j = 0; j < nh; ++j) if (!q.hc[j]) return RPQ_EINTERNAL;
+    for (int j = 0; j < q.n_c; ++j) if (!q.rm[j] || !q.rl[j]) return RPQ_EINTERNAL;
+  }
+  k_set_query<<<1, 32, 0, st>>>(s, q, d_kw);
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
@@ -1299,9 +1353,13 @@ void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Pr
   static const int enq_grid = one_wave_grid(k_enqueue, kEnqThreads);
   static const int exp_grid = one_wave_grid(k_expand, kExpThreads);
   static const int tgt_grid = num_sms() * 2;
+  if (prof) prof->tag_kind = kKindEnqueue;
   timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_enqueue<<<enq_grid, kEnqThreads, 0, st>>>(g, s, run); });
+  if (prof) prof->tag_kind = kKindTarget;
   if (run == 1) timed(prof, RPQ_PROF_ENQUEUE, st, [&] { k_target<<<tgt_grid, kTgtThreads, 0, st>>>(g, s); });
+  if (prof) prof->tag_kind = kKindExpand;
   timed(prof, RPQ_PROF_EXPAND, st, [&] { k_expand<<<exp_grid, kExpThreads, 0, st>>>(g, s, run, loop, in_graph ? 1 : 0); });
+  if (prof) prof->tag_kind = kKindOther;
 }
 
 // Top-w selection and, when the query has marginal keywords, the recovery.
@@ -1330,7 +1388,9 @@ int launch_query_body(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStre
                       bool stop_early) {
   auto levels = [&](int run) {
     for (int l = 0; l <= L; ++l) {
+      if (prof) { prof->tag_run = run; prof->tag_level = l; }
       launch_level(g, s, run, st, prof, 0, false);
+      if (prof) prof->tag_run = prof->tag_level = -1;
       if (!stop_early) continue;
       uint32_t done = 0;
       if (cudaStreamSynchronize(st) != cudaSuccess ||

@@ -1,15 +1,18 @@
 // Serving loop of librpq: continuous batching of radial-pattern queries.
 //
-// A server owns a set of search slots; each slot holds the device state of one
-// in-flight query (hit-level table, visited bytes, frontier bit maps and work
-// lists, about 60 bytes per graph node) and its own CUDA stream.  The number of
-// slots follows from the caller's device-memory budget: queries are admitted by
-// the memory their search state needs.  A submitted query starts at once when
-// a slot is free, otherwise it waits in a FIFO; every submit and poll call
-// collects finished queries (CUDA event per slot, no blocking) and admits
-// waiting queries into the slots they freed, so queries that arrive while
-// others run are overlapped on the device with them.  Each query runs exactly
-// the same kernels as rpq_search, so its result is the same alone or in the mix.
+// A server owns search slots and two pools of column pages.  A slot holds the
+// per-query state that does not depend on the keywords (visited bytes,
+// frontier bit maps, work lists, about 45 bytes per graph node) and its own
+// CUDA stream; a query's keyword columns are pages lent to it while it runs:
+// max(|C|, |M|) pages of the Node-Keyword Matrix (one byte per node each) and
+// |C| recovery pages (a CG mask and a list entry per node, 12 bytes per node
+// each).  So a query is admitted by the memory its own hit table needs: it
+// starts when a slot and its pages are free; otherwise it waits in a FIFO.
+// Every submit and poll call collects finished queries (CUDA event per slot,
+// no blocking), returns their pages and admits waiting queries, so queries
+// that arrive while others run are overlapped on the device with them.  Each
+// query runs exactly the same kernels as rpq_search, so its result is the
+// same alone or in the mix.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -38,8 +41,15 @@ struct rpq_server {
   std::vector<cudaEvent_t> done_ev;
   std::vector<Pending> running;      // per slot
   std::vector<bool> busy;
+  std::vector<std::vector<int32_t>> held_h, held_r;   // pages lent to each slot's query
   std::deque<Pending> waiting;
   std::deque<rpq_completion> finished;
+  uint8_t* hpool = nullptr;          // h_pages pages of hp bytes (Node-Keyword Matrix columns)
+  char* rpool = nullptr;             // r_pages pages: CG masks (8 * cap bytes) then node list (4 * cap)
+  int32_t h_pages = 0, r_pages = 0;
+  int64_t h_page_bytes = 0, r_page_bytes = 0, slot_fixed_bytes = 0;
+  std::vector<int32_t> h_free, r_free;
+  int32_t peak_running = 0;
   int64_t submitted = 0, completed = 0;
 };
 
@@ -49,7 +59,12 @@ static double seconds(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double>(b - a).count();
 }
 
-// Start waiting queries on free slots (in arrival order).
+// Keyword columns a query occupies: Node-Keyword Matrix pages (both runs
+// reuse them) and central recovery pages.
+static int h_cols(const QueryDev& q) { return std::max(q.n_c, q.n_m); }
+
+// Start waiting queries (in arrival order) while a slot and the head
+// query's pages are free.
 static int admit(rpq_server* sv) {
   size_t i = 0;
   while (!sv->waiting.empty()) {
@@ -68,6 +83,22 @@ static int admit(rpq_server* sv) {
     }
     while (i < sv->slots.size() && sv->busy[i]) ++i;
     if (i == sv->slots.size()) break;                 // every slot is busy
+    const int nh = h_cols(p.qv), nr = p.qv.n_c;
+    if (int(sv->h_free.size()) < nh || int(sv->r_free.size()) < nr) break;   // its pages are in use
+    for (int j = 0; j < nh; ++j) {
+      const int32_t pg = sv->h_free.back();
+      sv->h_free.pop_back();
+      sv->held_h[i].push_back(pg);
+      p.qv.hc[j] = sv->hpool + size_t(pg) * size_t(sv->h_page_bytes);
+    }
+    for (int j = 0; j < nr; ++j) {
+      const int32_t pg = sv->r_free.back();
+      sv->r_free.pop_back();
+      sv->held_r[i].push_back(pg);
+      char* base = sv->rpool + size_t(pg) * size_t(sv->r_page_bytes);
+      p.qv.rm[j] = reinterpret_cast<unsigned long long*>(base);
+      p.qv.rl[j] = reinterpret_cast<uint32_t*>(base + sizeof(unsigned long long) * sv->slots[i]->d.cap);
+    }
     const int rc = start_query(sv->kg, sv->slots[i], p.qv);
     if (rc != RPQ_OK) return rc;
     const cudaError_t e = cudaEventRecord(sv->done_ev[i], sv->slots[i]->st);
@@ -75,7 +106,30 @@ static int admit(rpq_server* sv) {
     sv->running[i] = p;
     sv->busy[i] = true;
     sv->waiting.pop_front();
+    int32_t r = 0;
+    for (bool b : sv->busy) r += b;
+    sv->peak_running = std::max(sv->peak_running, r);
   }
+  return RPQ_OK;
+}
+
+// Return the pages of slot i's finished query.  Recovery pages come back with
+// their CG masks at zero (the recovery clears every mask it set); after a
+// failed query they are cleared here.
+static int release_pages(rpq_server* sv, size_t i, bool failed) {
+  if (failed) {
+    for (int32_t pg : sv->held_r[i]) {
+      const cudaError_t e = cudaMemsetAsync(sv->rpool + size_t(pg) * size_t(sv->r_page_bytes), 0,
+                                            sizeof(unsigned long long) * sv->slots[i]->d.cap, sv->slots[i]->st);
+      if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)); return RPQ_ECUDA; }
+    }
+    const cudaError_t e = cudaStreamSynchronize(sv->slots[i]->st);
+    if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e)); return RPQ_ECUDA; }
+  }
+  sv->h_free.insert(sv->h_free.end(), sv->held_h[i].begin(), sv->held_h[i].end());
+  sv->r_free.insert(sv->r_free.end(), sv->held_r[i].begin(), sv->held_r[i].end());
+  sv->held_h[i].clear();
+  sv->held_r[i].clear();
   return RPQ_OK;
 }
 
@@ -93,6 +147,8 @@ static int collect(rpq_server* sv, bool block) {
       c.tag = sv->running[i].tag;
       c.status = finish_query(sv->kg, sv->slots[i], c.res, &c.n_res, &c.stats);
       c.latency_s = seconds(sv->running[i].t_submit, Clock::now());
+      const int prc = release_pages(sv, i, c.status != RPQ_OK);
+      if (prc != RPQ_OK) return prc;
       sv->busy[i] = false;
       sv->finished.push_back(c);
       ++sv->completed;
@@ -112,19 +168,55 @@ using namespace rpq;
 
 extern "C" {
 
-int rpq_server_create(rpq_kg* kg, int64_t budget_bytes, int32_t max_slots, rpq_server** out) {
-  if (!kg || !out || max_slots < 1) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
+// Slots and column pages a server holds: slots alone may not hold all
+// columns of every query at once, so the budget is split for queries of
+// about 4 central keywords and 6 Node-Keyword Matrix columns on average: each
+// slot comes with 6 matrix pages and the rest of the budget buys recovery
+// pages (at least kMaxCols of each kind, so that every query fits).
+static void size_server(const rpq_kg* kg, int64_t budget, int32_t max_slots, int32_t* slots, int32_t* h_pages,
+                        int32_t* r_pages) {
+  const int64_t f = slot_bytes(kg, false);
+  const int64_t h = int64_t((size_t(kg->dev.n) + 15) / 16 * 16);
+  const int64_t r = (12 * int64_t(std::max<int32_t>(kg->dev.n, 1)) + 255) / 256 * 256;
+  int64_t s = std::max<int64_t>(1, budget / (f + 6 * h + 4 * r));
+  s = std::min<int64_t>(s, max_slots);
+  const int64_t hp = std::max<int64_t>(kMaxCols, 6 * s);
+  const int64_t rest = budget - s * f - hp * h - 16;
+  const int64_t rp = std::min<int64_t>(std::max<int64_t>(kMaxCols, rest / r), int64_t(kMaxCols) * s);
+  *slots = int32_t(s);
+  *h_pages = int32_t(hp);
+  *r_pages = int32_t(rp);
+}
+
+int rpq_server_create_sized(rpq_kg* kg, int32_t n_slots, int32_t h_pages, int32_t r_pages, rpq_server** out) {
+  if (!kg || !out || n_slots < 1 || n_slots > 4096 || h_pages < kMaxCols || r_pages < kMaxCols ||
+      h_pages > (1 << 20) || r_pages > (1 << 20)) {
+    set_error(RPQ_EINVAL, "bad argument (need 1 <= n_slots <= 4096 and %d <= pages <= 2^20)", kMaxCols);
+    return RPQ_EINVAL;
+  }
   *out = nullptr;
   rpq_server* sv = new rpq_server();
   sv->kg = kg;
-  int rc = RPQ_OK;
-  int64_t used = 0;
-  while (int32_t(sv->slots.size()) < max_slots) {
+  const size_t cap = size_t(std::max<int32_t>(kg->dev.n, 1));
+  sv->h_page_bytes = int64_t((size_t(kg->dev.n) + 15) / 16 * 16);
+  sv->r_page_bytes = int64_t((12 * cap + 255) / 256 * 256);
+  sv->slot_fixed_bytes = slot_bytes(kg, false);
+  int64_t pool_bytes = 0;
+  int rc = alloc_device((void**)&sv->hpool, size_t(sv->h_page_bytes) * size_t(h_pages) + 16, &pool_bytes);
+  if (rc == RPQ_OK) rc = alloc_device((void**)&sv->rpool, size_t(sv->r_page_bytes) * size_t(r_pages), &pool_bytes);
+  if (rc == RPQ_OK && cudaMemset(sv->rpool, 0, size_t(sv->r_page_bytes) * size_t(r_pages)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error(RPQ_ECUDA, "page pool clear failed");
+    rc = RPQ_ECUDA;
+  }
+  sv->h_pages = h_pages;
+  sv->r_pages = r_pages;
+  for (int32_t i = h_pages - 1; i >= 0; --i) sv->h_free.push_back(i);
+  for (int32_t i = r_pages - 1; i >= 0; --i) sv->r_free.push_back(i);
+  while (rc == RPQ_OK && int32_t(sv->slots.size()) < n_slots) {
     Slot* s = nullptr;
-    rc = create_slot(kg, &s);
+    rc = create_slot(kg, &s, false);
     if (rc != RPQ_OK) break;
-    if (!sv->slots.empty() && used + s->bytes > budget_bytes) { destroy_slot(s); break; }
-    used += s->bytes;
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       destroy_slot(s);
@@ -135,24 +227,44 @@ int rpq_server_create(rpq_kg* kg, int64_t budget_bytes, int32_t max_slots, rpq_s
     sv->slots.push_back(s);
     sv->done_ev.push_back(ev);
   }
-  if (sv->slots.empty() || (rc != RPQ_OK && rc != RPQ_ENOMEM)) {
+  if (rc != RPQ_OK) {
     rpq_server_destroy(sv);
-    return rc != RPQ_OK ? rc : RPQ_ENOMEM;
+    return rc;
   }
   sv->running.resize(sv->slots.size());
   sv->busy.assign(sv->slots.size(), false);
+  sv->held_h.resize(sv->slots.size());
+  sv->held_r.resize(sv->slots.size());
   *out = sv;
   return RPQ_OK;
+}
+
+int rpq_server_create(rpq_kg* kg, int64_t budget_bytes, int32_t max_slots, rpq_server** out) {
+  if (!kg || !out || max_slots < 1) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
+  int32_t s = 0, hp = 0, rp = 0;
+  size_server(kg, budget_bytes, std::min(max_slots, 4096), &s, &hp, &rp);
+  return rpq_server_create_sized(kg, s, hp, rp, out);
 }
 
 int rpq_server_info(const rpq_server* sv, int32_t* n_slots, int64_t* slot_bytes, int32_t* n_running, int32_t* n_waiting) {
   if (!sv) { set_error(RPQ_EINVAL, "NULL server"); return RPQ_EINVAL; }
   if (n_slots) *n_slots = int32_t(sv->slots.size());
-  if (slot_bytes) *slot_bytes = sv->slots.empty() ? 0 : sv->slots[0]->bytes;
+  if (slot_bytes) *slot_bytes = sv->slot_fixed_bytes;
   int32_t r = 0;
   for (bool b : sv->busy) r += b;
   if (n_running) *n_running = r;
   if (n_waiting) *n_waiting = int32_t(sv->waiting.size());
+  return RPQ_OK;
+}
+
+int rpq_server_pages(const rpq_server* sv, int32_t* h_pages, int64_t* h_page_bytes, int32_t* r_pages,
+                     int64_t* r_page_bytes, int32_t* peak_running) {
+  if (!sv) { set_error(RPQ_EINVAL, "NULL server"); return RPQ_EINVAL; }
+  if (h_pages) *h_pages = sv->h_pages;
+  if (h_page_bytes) *h_page_bytes = sv->h_page_bytes;
+  if (r_pages) *r_pages = sv->r_pages;
+  if (r_page_bytes) *r_page_bytes = sv->r_page_bytes;
+  if (peak_running) *peak_running = sv->peak_running;
   return RPQ_OK;
 }
 
@@ -249,6 +361,8 @@ int rpq_server_destroy(rpq_server* sv) {
     destroy_slot(sv->slots[i]);
     if (i < sv->done_ev.size()) cudaEventDestroy(sv->done_ev[i]);
   }
+  cudaFree(sv->hpool);
+  cudaFree(sv->rpool);
   delete sv;
   return RPQ_OK;
 }

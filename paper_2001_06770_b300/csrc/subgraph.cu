@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(kSwThreads) k_sg_sweep(DevKG g, DevSlot s, int
   const int j = int(blockIdx.x);
   const uint32_t nsel = c->nsel;
   if (j >= nt || nsel == 0) return;
-  const uint8_t* Hj = s.H + size_t(j) * s.hp;
-  unsigned long long* rmask = s.rmask + size_t(j) * s.cap;
-  uint32_t* rlist = s.rlist + size_t(j) * s.cap;
+  const uint8_t* Hj = hcol(*s.q, j);
+  unsigned long long* rmask = rmcol(*s.q, j);
+  uint32_t* rlist = rlcol(*s.q, j);
   __shared__ uint32_t s_off[kSwThreads];
   __shared__ uint32_t s_rb[kSwThreads];
   __shared__ unsigned long long s_m[kSwThreads];
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kSgThreads) k_sg_edges(DevKG g, DevSlot s, SgD
       const uint32_t vb = vis_byte(s.vis, qn);
       uint32_t hmax = 0;
       for (int j = 0; j < nt; ++j)
-        if (((vb >> j) & 1u) && s.rmask[size_t(j) * s.cap + qn]) hmax = max(hmax, uint32_t(s.H[size_t(j) * s.hp + qn]));
+        if (((vb >> j) & 1u) && rmcol(q, j)[qn]) hmax = max(hmax, uint32_t(hcol(q, j)[qn]));
       if (hmax > 0) {
         rb = g.row_ptr[qn];
         len = seg_at(g, qn, rb, g.row_ptr[qn + 1], hmax) - rb;
@@ -273,9 +273,9 @@ __global__ void __launch_bounds__(kSgThreads) k_sg_edges(DevKG g, DevSlot s, SgD
       unsigned long long mask = 0;
       for (int j = 0; j < nt; ++j) {
         if (!((vq >> j) & 1u) || !((vn >> j) & 1u)) continue;
-        const unsigned long long m = s.rmask[size_t(j) * s.cap + qq];
+        const unsigned long long m = rmcol(q, j)[qq];
         if (!m) continue;
-        const uint32_t hq = s.H[size_t(j) * s.hp + qq], hn = s.H[size_t(j) * s.hp + nb];
+        const uint32_t hq = hcol(q, j)[qq], hn = hcol(q, j)[nb];
         const uint32_t lam = a > hn ? a : hn;
         if (lam + 1 != hq || stopped_before(s, nb, lam)) continue;
         mask |= m;
@@ -298,12 +298,12 @@ __global__ void k_sg_nodes(DevSlot s, SgDev sg, int run) {
     const uint32_t v = s.ulist[i];
     const unsigned long long m = s.vmask[v];
     s.vmask[v] = 0;
-    for (int j = 0; j < nt; ++j) s.rmask[size_t(j) * s.cap + v] = 0;
+    for (int j = 0; j < nt; ++j) rmcol(q, j)[v] = 0;
     emit(sg, m, v, (run == 0 ? kSgVc : kSgVm) << kNodeBits);
     if (run != 0) continue;
     const uint32_t vb = vis_byte(s.vis, v);
     bool holds = false;
-    for (int j = 0; j < nt; ++j) holds |= ((vb >> j) & 1u) && s.H[size_t(j) * s.hp + v] == 0;
+    for (int j = 0; j < nt; ++j) holds |= ((vb >> j) & 1u) && hcol(q, j)[v] == 0;
     if (!holds) continue;
     emit(sg, m, v, kSgVcKw << kNodeBits);
     for (unsigned long long b = m; b; b &= b - 1) {
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kPtcThreads) k_sg_ptc(DevSlot s, SgDev sg) {
     const uint32_t vb = vis_byte(s.vis, v);
     uint32_t hold = 0;
     for (int j = 0; j < nm; ++j)
-      if (((vb >> j) & 1u) && s.H[size_t(j) * s.hp + v] == 0) hold |= 1u << j;
+      if (((vb >> j) & 1u) && hcol(*s.q, j)[v] == 0) hold |= 1u << j;
     atomicExch(&lab[h], v);
     if (hold) atomicOr(&flg[h], hold);
   }

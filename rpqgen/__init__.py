@@ -188,6 +188,10 @@ CONFIGS = {
     "mid": dict(kind="rmat", scale=18, nedges=3_000_000, kw=(1, 4), vocab=30000, kw_zipf=1.05),
     "cl_small": dict(kind="chunglu", n=300_000, nedges=2_000_000, beta=2.1, max_degree=2e4,
                      kw=(1, 4), vocab=40000, kw_zipf=1.0),
+    # profiling case of the large graph's kind at a tenth of its size: the
+    # adjacency (about 3e8 bytes) is still larger than L2
+    "cl_5m": dict(kind="chunglu", n=5_000_000, nedges=40_000_000, beta=2.1, max_degree=1e5,
+                  kw=(1, 4), vocab=500_000, kw_zipf=1.0),
 }
 
 
@@ -315,7 +319,7 @@ def workload_queries(name: str, ds: Dataset, seed: int = 1):
         return queries_uniform(1, (2, 2), (2, 2), (50, 500), 10, 6, seed)
     if name == "medium":
         return queries_uniform(64, (2, 4), (0, 4), (100, 20000), 20, 8, seed)
-    if name == "large":
+    if name in ("large", "cl_5m"):
         return queries_uniform(256, (3, 3), (3, 3), (100, 20000), 20, 8, seed)
     if name == "batched":
         return queries_mixed(ds, 4096, seed=seed)

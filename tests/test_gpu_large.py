@@ -1,7 +1,18 @@
 """Full-size checks on the large workload (Chung-Lu, 5e7 nodes, 7.6e8 CSR
-entries, queries of 3 + 3 keywords, k = 20, L = 8).  The serial oracle needs
-minutes per query there, so these tests check properties that hold at any
-size, on the device's own trace, plus equality between the search paths:
+entries, queries of 3 + 3 keywords, k = 20, L = 8, and the batched
+workload's uneven shapes with head and tail keywords on the same graph).
+
+Against the oracle (its own activation levels and a graph prepared once;
+about half a minute of one host core per query, the sampled queries run in
+parallel): two queries of the one-at-a-time workload element by element -
+results, both runs' hit-level tables, the CG set, the selected CGs, V_C of
+each, E_act and the stop levels - and two queries of the batched mix, one
+with the most head keywords (postings over 10^5 nodes, rows of the hub
+level index) and one of tail keywords only, by results, E_act and levels
+through the one-at-a-time, batched and traced paths.
+
+Properties that hold at any size, on the device's own trace, plus equality
+between the search paths:
 
 * hit levels (Theorem 5 with the stop rules): a sampled node's level h > 0 has
   a parent u with max(h_u, a) + 1 = h that had not stopped, no neighbour
@@ -12,14 +23,19 @@ size, on the device's own trace, plus equality between the search paths:
 * Eq. 6 and Definition 6: scores and the (S^r, id) order of the results;
 * the graph-replayed search, the trace and the batch give the same results.
 """
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
+import oracle
 import paper_2001_06770_b300 as rpq
 import rpqgen
-from tests.gpu_common import INF, check_levels
+from tests.gpu_common import INF, check_levels, results_match
 
 pytestmark = pytest.mark.gpu
+
+HEAD_MIN = 100_000    # postings of a head keyword in the batched workload
 
 @pytest.fixture(scope="module")
 def large():
@@ -81,3 +97,86 @@ def test_large_paths_agree(large):
     tr = kg.trace(sample[1].central, sample[1].marginal, sample[1].k, sample[1].max_depth, sample[1].gamma)
     res, _ = kg.search(sample[1].central, sample[1].marginal, sample[1].k, sample[1].max_depth, sample[1].gamma)
     assert res.tobytes() == tr["results"].tobytes()
+
+
+def mixed_pair(ds):
+    """From the first 400 queries of the batched workload: the one with the
+    most head keywords (marginal keywords included) and one with tail keywords
+    only, both with marginal keywords."""
+    sizes = np.diff(ds.kw_ptr)
+    mq = rpqgen.workload_queries("batched", ds)[:400]
+    heads = [sum(int(sizes[k] > HEAD_MIN) for k in q.central + q.marginal) for q in mq]
+    cand = [i for i in range(len(mq)) if mq[i].marginal]
+    heavy = max(cand, key=lambda i: (heads[i], len(mq[i].central) + len(mq[i].marginal), -i))
+    tail = next(i for i in cand if heads[i] == 0)
+    return mq[heavy], mq[tail], heads[heavy]
+
+
+@pytest.fixture(scope="module")
+def large_oracle(large):
+    """The oracle's answers for two one-at-a-time queries (with both runs'
+    hit-level tables) and the two batched-mix queries, computed in parallel."""
+    ds, kg, adj, qs = large
+    act = oracle.dataset_activation(ds, detail=False)
+    pg = oracle.PreparedGraph(ds, act.a)
+    heavy, tail, nhead = mixed_pair(ds)
+    jobs = [(qs[0], True), (qs[1], True), (heavy, False), (tail, False)]
+
+    def one(job):
+        q, tables = job
+        return oracle.search(None, None, q.central, q.marginal, q.k, q.max_depth, q.gamma, prepared=pg,
+                             trace=False, subgraphs=False, tables=tables)
+
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        out = list(ex.map(one, jobs))
+    pg.close()
+    del act
+    yield [q for q, _ in jobs], out, nhead
+
+
+def test_large_trace_equals_oracle(large, large_oracle):
+    """One-at-a-time queries of the large workload, element by element."""
+    ds, kg, adj, qs = large
+    queries, orcs, _ = large_oracle
+    for q, orc in zip(queries[:2], orcs[:2]):
+        tr = kg.trace(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        results_match(tr["results"], orc)
+        assert np.array_equal(tr["h_central"], orc.central.h), "central hit levels differ"
+        gcg = sorted((int(x) >> 8, int(x) & 0xff) for x in tr["cgs"])
+        assert gcg == sorted(zip(orc.cg_node.tolist(), orc.cg_score.tolist())), "CG sets differ"
+        assert tr["selected"].tolist() == orc.selected.tolist()
+        st = tr["stats"]
+        assert st["e_act_central"] == orc.central.e_act
+        assert st["levels_central"] == orc.central.last_level
+        if orc.marginal is not None:
+            for g in range(len(orc.selected)):
+                assert tr["vc"][g].tolist() == orc.vc_kw[g].tolist(), f"V_C of CG {g} differs"
+            assert np.array_equal(tr["h_marginal"], orc.marginal.h), "marginal hit levels differ"
+            assert st["e_act_marginal"] == orc.marginal.e_act
+            assert st["levels_marginal"] == orc.marginal.last_level
+        # the graph-replayed search (it may skip the final marginal expansion)
+        res, st1 = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        results_match(res, orc)
+        assert st1["e_act_central"] == orc.central.e_act
+        if orc.marginal is not None:
+            assert st1["e_act_marginal"] == orc.marginal.e_act
+
+
+def test_large_mixed_shapes_equal_oracle(large, large_oracle):
+    """Batched-mix queries (a head-heavy one reaching hub rows from posting
+    lists of 10^5+ nodes, and a tail one): results, E_act and levels through
+    the one-at-a-time and batched paths."""
+    ds, kg, adj, qs = large
+    queries, orcs, nhead = large_oracle
+    assert nhead >= 2
+    batch = kg.search_batch(queries[2:])
+    for q, orc, (bres, bst, status) in zip(queries[2:], orcs[2:], batch):
+        assert status == 0
+        res, st = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        results_match(res, orc)
+        results_match(bres, orc)
+        assert st["e_act_central"] == orc.central.e_act == bst["e_act_central"]
+        assert st["levels_central"] == orc.central.last_level
+        if orc.marginal is not None:
+            assert st["e_act_marginal"] == orc.marginal.e_act == bst["e_act_marginal"]
+            assert st["levels_marginal"] == orc.marginal.last_level

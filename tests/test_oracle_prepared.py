@@ -43,6 +43,15 @@ def test_prepared_graph_equals_one_call(tiny_ds, tiny_act):
         for q, r in zip(qs, ref):
             got = oracle.search(None, None, q.central, q.marginal, q.k, q.max_depth, q.gamma, prepared=pg)
             _same(got, r, True, True)
+        # hit-level tables without the frontier lists
+        for q, r in zip(qs[:3], ref):
+            got = oracle.search(None, None, q.central, q.marginal, q.k, q.max_depth, q.gamma, prepared=pg,
+                                trace=False, subgraphs=False, tables=True)
+            _same(got, r, False, False)
+            for ra, rb in ((got.central, r.central), (got.marginal, r.marginal)):
+                if ra is not None:
+                    assert ra.frontiers is None
+                    assert np.array_equal(ra.h, rb.h) and np.array_equal(ra.stop, rb.stop)
         # several threads on one prepared graph, counts only
         many = oracle.search_many(pg, qs, threads=4)
         for got, r in zip(many, ref):
