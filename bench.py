@@ -364,6 +364,14 @@ def expand_roofline(kg, qs, stats, workload="medium"):
     return roof, {k: v[0] for k, v in prof.items()}
 
 
+def step_transfer_bytes(qs):
+    """Host-to-device and device-to-host bytes of the queries' host-API calls
+    (the library reports the per-call sizes)."""
+    import paper_2001_06770_b300 as rpq
+    per = [rpq.transfer_bytes(q.k) for q in qs]
+    return sum(h for h, _ in per), sum(d for _, d in per)
+
+
 def base_line(args, ws, wl, value, t_step, steps):
     return {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -464,8 +472,7 @@ def run_single(args, ws, rank, local, wl, ds, qs, kg):
             lat.append(time.perf_counter() - t)
     t_e2e = allmax(ws, time.perf_counter() - t0)
     e2e = ws * nq * args.steps / t_e2e
-    h2d = 88 * nq                                  # parameter block with the keyword ids, per query
-    d2h = sum(24 * q.k + 600 for q in qs)          # results + control block (600 B), per query
+    h2d, d2h = step_transfer_bytes(qs)            # query records in, control blocks with results out
 
     # batched: all queries in one rpq_search_batch call (concurrent slots)
     kg.search_batch(qs)
@@ -589,8 +596,8 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
         "one_at_a_time_qps": one_qps,
         "batched_vs_one_at_a_time": value / (ws * one_qps),
         "equal_results_checked": len(sample),
-        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 88 * nq,
-                "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": step_transfer_bytes(qs)[0],
+                "d2h_bytes_per_step": step_transfer_bytes(qs)[1]},
         "gpu_launches": sum(s["kernels"] for s in stats) * args.steps,
         "roofline": roof, "kernel_ms_per_step_sample": kms,
         "oracle_checked": {"batched": len(idx)},
@@ -662,8 +669,8 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
         "one_at_a_time_qps": one_qps,
         "served_vs_one_at_a_time": best["qps"] / one_qps,
         "equal_results_checked": len(sample),
-        "e2e": {"value": ws * best["qps"], "unit": "queries/s", "h2d_bytes_per_step": 88 * nq,
-                "d2h_bytes_per_step": sum(24 * q.k + 600 for q in qs)},
+        "e2e": {"value": ws * best["qps"], "unit": "queries/s", "h2d_bytes_per_step": step_transfer_bytes(qs)[0],
+                "d2h_bytes_per_step": step_transfer_bytes(qs)[1]},
         "gpu_launches": None, "roofline": None,
         "oracle_checked": {"served": len(sample)},
         "cpu_baseline": dict(cpu, sample=f"{len(sample)} of the {nq} queries (evenly spaced), serial C oracle, "

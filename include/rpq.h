@@ -468,6 +468,12 @@ int rpq_server_destroy(rpq_server *srv);
 int rpq_topk_keys_noalloc(const uint32_t *d_keys, uint32_t n, int32_t k, uint32_t *d_out, uint32_t *d_n_out,
                           void *stream);
 
+/* Host <-> device bytes of one rpq_search call with k results: *h2d is the
+ * query record the launch carries (keyword ids and parameters), *d2h the one
+ * copy that returns the control block with the results.  Either pointer may
+ * be NULL.  Errors: RPQ_EINVAL (k out of range). */
+int rpq_transfer_bytes(int32_t k, int64_t *h2d, int64_t *d2h);
+
 /* -------------------------------------------------------------- messages */
 const char *rpq_strerror(int code);
 const char *rpq_last_error(void);

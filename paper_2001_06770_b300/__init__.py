@@ -31,7 +31,7 @@ SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_se
            "rpq_trace", "rpq_search_subgraphs", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
            "rpq_profile_read", "rpq_profile_levels", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_create_sized", "rpq_server_info", "rpq_server_pages",
            "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
-           "rpq_get_tuning", "rpq_set_tuning", "rpq_autotune",
+           "rpq_get_tuning", "rpq_set_tuning", "rpq_autotune", "rpq_transfer_bytes",
            "rpq_strerror", "rpq_last_error"]
 PROF_CLASSES = ["setup", "enqueue", "expand", "topk", "recover", "results"]
 
@@ -163,6 +163,7 @@ def lib():
         L.rpq_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
         L.rpq_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
         L.rpq_autotune.argtypes = [P, P, i32, i32, ctypes.POINTER(Tuning)]
+        L.rpq_transfer_bytes.argtypes = [i32, P, P]
         L.rpq_strerror.argtypes = [ctypes.c_int]
         L.rpq_strerror.restype = ctypes.c_char_p
         L.rpq_last_error.restype = ctypes.c_char_p
@@ -180,6 +181,13 @@ def _check(rc: int):
 def _ptr(a):
     # the address as a Python int: every argument and field it feeds is c_void_p
     return None if a is None else a.ctypes.data
+
+
+def transfer_bytes(k: int):
+    """(host-to-device, device-to-host) bytes of one rpq_search with k results."""
+    h, d = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().rpq_transfer_bytes(int(k), ctypes.byref(h), ctypes.byref(d)))
+    return h.value, d.value
 
 
 def topk_keys_noalloc(d_keys: int, n: int, k: int, d_out: int, d_n_out: int, stream: int = 0):

@@ -546,8 +546,10 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
     for (int64_t i = 0; i <= d->n_kw; ++i) kp[i] = uint32_t(d->kw_ptr[i]);
     rc = alloc_device((void**)&kg->d_kw_ptr, sizeof(uint32_t) * kp.size(), &kg->device_bytes);
     if (rc == RPQ_OK) rc = alloc_device((void**)&kg->d_kw_nodes, sizeof(int32_t) * size_t(std::max<int64_t>(npost, 1)), &kg->device_bytes);
+    std::vector<int32_t> kn(size_t(std::max<int64_t>(npost, 0)));
+    for (int64_t i = 0; i < npost; ++i) kn[size_t(i)] = kg->int_of[size_t(d->kw_nodes[i])];   // internal ids
     if (rc == RPQ_OK && (cudaMemcpy(kg->d_kw_ptr, kp.data(), sizeof(uint32_t) * kp.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-                         (npost > 0 && cudaMemcpy(kg->d_kw_nodes, d->kw_nodes, sizeof(int32_t) * size_t(npost), cudaMemcpyHostToDevice) != cudaSuccess))) {
+                         (npost > 0 && cudaMemcpy(kg->d_kw_nodes, kn.data(), sizeof(int32_t) * size_t(npost), cudaMemcpyHostToDevice) != cudaSuccess))) {
       set_error(RPQ_ECUDA, "postings upload failed");
       rc = RPQ_ECUDA;
     }
@@ -563,6 +565,8 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
   kg->dev.n_kw = d->n_kw;
   kg->dev.kw_ptr = kg->d_kw_ptr;
   kg->dev.kw_nodes = kg->d_kw_nodes;
+  kg->dev.ext_of = kg->d_ext_of;
+  kg->dev.int_of = kg->d_int_of;
   *out = kg;
   return RPQ_OK;
 }
@@ -573,16 +577,14 @@ int rpq_free_kg(rpq_kg* kg) {
   free_subgraph_scratch(kg);
   delete kg->prof;
   cudaFree(kg->d_row_ptr); cudaFree(kg->d_adj); cudaFree(kg->d_amax); cudaFree(kg->d_lvx); cudaFree(kg->d_lvx_long);
-  cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes);
+  cudaFree(kg->d_kw_ptr); cudaFree(kg->d_kw_nodes); cudaFree(kg->d_ext_of); cudaFree(kg->d_int_of);
   delete kg;
   return RPQ_OK;
 }
 
 int rpq_kg_export(const rpq_kg* kg, uint32_t* adj, uint8_t* amax) {
   if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
-  if (adj && kg->m2) RPQ_CUDA(cudaMemcpy(adj, kg->d_adj, sizeof(uint32_t) * size_t(kg->m2), cudaMemcpyDeviceToHost));
-  if (amax) RPQ_CUDA(cudaMemcpy(amax, kg->d_amax, size_t(kg->dev.n), cudaMemcpyDeviceToHost));
-  return RPQ_OK;
+  return export_graph(kg, adj, amax);
 }
 
 int rpq_kg_info(const rpq_kg* kg, int32_t* n, int64_t* m2, int64_t* device_bytes) {
@@ -674,6 +676,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   Ctl c{};
   auto frontiers = [&](uint32_t from, uint32_t to, int64_t* ptr, int32_t* dst, int64_t cap, int32_t* levels) {
     std::vector<uint32_t> e(qlog.begin() + from, qlog.begin() + to);
+    for (uint32_t& x : e) x = (x & ~kNodeMask) | uint32_t(kg->ext_of[x & kNodeMask]);   // caller ids
     std::sort(e.begin(), e.end());   // by level, then node
     int maxl = -1;
     for (uint32_t x : e) maxl = std::max<int>(maxl, int(x >> kNodeBits));
@@ -691,9 +694,11 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   };
   auto hmat = [&](uint8_t* dst, int nt) {
     if (!dst) return;
-    for (size_t v = 0; v < n; ++v)
+    for (size_t v = 0; v < n; ++v) {
+      const size_t u = size_t(kg->ext_of[v]);   // row of the caller's node
       for (int j = 0; j < nt; ++j)
-        dst[v * size_t(nt) + size_t(j)] = ((vis[v] >> j) & 1) ? H[size_t(j) * d.hp + v] : kInf;
+        dst[u * size_t(nt) + size_t(j)] = ((vis[v] >> j) & 1) ? H[size_t(j) * d.hp + v] : kInf;
+    }
   };
   auto fail = [&](int code) { cudaFree(d_qlog); return code; };
 #define TC(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) { set_error(RPQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); return fail(RPQ_ECUDA); } } while (0)
@@ -725,7 +730,8 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
   {
     std::vector<uint32_t> vcl(std::min<uint32_t>(c.nvc, d.cap));
     if (!vcl.empty()) TC(cudaMemcpy(vcl.data(), d.vcl, sizeof(uint32_t) * vcl.size(), cudaMemcpyDeviceToHost));
-    std::vector<int64_t> vc(vcl.begin(), vcl.end());
+    std::vector<int64_t> vc;
+    for (uint32_t x : vcl) vc.push_back(int64_t((x & ~kNodeMask) | uint32_t(kg->ext_of[x & kNodeMask])));
     std::sort(vc.begin(), vc.end());
     tr->n_vc = int64_t(vc.size());
     if (tr->vc) for (size_t i = 0; i < vc.size() && int64_t(i) < tr->vc_cap; ++i) tr->vc[i] = vc[i];
@@ -902,6 +908,13 @@ int rpq_profile_levels(rpq_kg* kg, rpq_level_profile* out, int32_t cap, int32_t*
   if (n) memcpy(out, v.data(), sizeof(rpq_level_profile) * n);
   *n_out = int32_t(v.size());
   if (reset) kg->prof->levels.clear();
+  return RPQ_OK;
+}
+
+int rpq_transfer_bytes(int32_t k, int64_t* h2d, int64_t* d2h) {
+  if (k < 1 || k > kMaxK) { set_error(RPQ_EINVAL, "need 1 <= k <= %d", kMaxK); return RPQ_EINVAL; }
+  if (h2d) *h2d = int64_t(sizeof(QueryDev));
+  if (d2h) *d2h = int64_t(kCtlBytes + sizeof(rpq_result) * size_t(k));
   return RPQ_OK;
 }
 

@@ -18,9 +18,21 @@
 //                  global min/max of cnt
 //   k_presence     marks the counts that occur
 //   k_pack         adj(e) = level(cnt(e)) << 26 | neighbour
-//   k_sort_small / k_sort_large   per-row sort by (level, neighbour): rank
-//                  sort in a warp, stable counting sort by level in a block;
+//   k_relabel      rows and neighbours renumbered to the internal ids
+//   k_sort_small / k_sort_pass   per-row sort by (level, neighbour): rank
+//                  sort in a warp; for longer rows, stable counting sorts by
+//                  6-bit digits in a block (neighbour bits, then the level);
 //                  both also write amax(u)
+//
+// Internal node ids.  The search numbers nodes by decreasing degree (ties by
+// the caller's id): on a power-law graph most CSR entries point at the few
+// high-degree nodes, and with this numbering their visited bytes, hit levels
+// and bit-map words share a few hundred kilobytes of cache lines instead of
+// being scattered over the whole per-node arrays.  Node ids cross the
+// boundary in the caller's numbering: postings are renumbered at load, and
+// results, traces, subgraphs and exports are given back in caller ids.  The
+// identification keys of CGs carry caller ids, so every tie between equal
+// scores is still broken by the caller's node id.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -163,9 +175,34 @@ __global__ void k_pack(uint32_t m2, uint32_t* __restrict__ cnt_adj, const int32_
   }
 }
 
-// Rows of <= 32 entries: rank sort in a warp (values are distinct in a row).
-__global__ void k_sort_small(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ in,
-                             uint32_t* __restrict__ out, uint8_t* __restrict__ amax) {
+// Renumbered rows: entry e of caller row u goes to row to_new[u] of the
+// renumbered CSR (same offset in the row) with its neighbour renumbered.
+// Also used the other way round (to_new = internal -> caller ids) for exports.
+// One warp per 32 consecutive entries, rows located as in k_count.
+__global__ void k_relabel(int32_t n, uint32_t m2, const uint32_t* __restrict__ row_ptr,
+                          const uint32_t* __restrict__ new_row_ptr, const int32_t* __restrict__ to_new,
+                          const uint32_t* __restrict__ in, uint32_t* __restrict__ out) {
+  const uint32_t lane = lane_id();
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < m2; base += nwarps * 32) {
+    const uint32_t r0 = row_of(row_ptr, 0, uint32_t(n - 1), uint32_t(base));
+    const uint32_t last = uint32_t(base + 31 < int64_t(m2) ? base + 31 : int64_t(m2) - 1);
+    const uint32_t r1 = row_of(row_ptr, r0, uint32_t(n - 1), last);
+    const uint32_t e = uint32_t(base) + lane;
+    if (e < m2) {
+      const uint32_t u = row_of(row_ptr, r0, r1, e);
+      const uint32_t x = in[e];
+      const uint32_t nu = uint32_t(to_new[u]);
+      out[new_row_ptr[nu] + (e - row_ptr[u])] = (x & ~kNodeMask) | uint32_t(to_new[x & kNodeMask]);
+    }
+  }
+}
+
+// Rows of <= 32 entries: rank sort in a warp (values are distinct in a row);
+// in place is allowed (every lane reads before any lane writes).
+__global__ void k_sort_small(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* in,
+                             uint32_t* out, uint8_t* __restrict__ amax) {
   const uint32_t lane = lane_id();
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -178,16 +215,18 @@ __global__ void k_sort_small(int32_t n, const uint32_t* __restrict__ row_ptr, co
     if (lane < d) out[rb + rank] = x;
     uint32_t lv = lane < d ? (x >> kNodeBits) : 0u;
     for (int o = 16; o; o >>= 1) lv = max(lv, __shfl_xor_sync(0xffffffffu, lv, o));
-    if (lane == 0) amax[u] = uint8_t(lv);
+    if (lane == 0 && amax) amax[u] = uint8_t(lv);
   }
 }
 
-// Rows of > 32 entries: stable counting sort by level (rows arrive sorted by
-// neighbour id, so the result is sorted by (level, neighbour)).  One block of
+// Rows of > 32 entries: stable counting sort by the 6-bit digit at `shift`
+// (a pass of a least-significant-digit radix sort: the neighbour bits at
+// shifts 0, 6, 12, 18, 24, then the level at 26 gives (level, neighbour)
+// order; the level pass also writes amax when it is given).  One block of
 // kSortWarps warps per row; chunks of blockDim entries are placed in order.
 __global__ void __launch_bounds__(kSortWarps * 32)
-k_sort_large(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ in,
-             uint32_t* __restrict__ out, uint8_t* __restrict__ amax) {
+k_sort_pass(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __restrict__ in,
+            uint32_t* __restrict__ out, uint32_t shift, uint8_t* __restrict__ amax) {
   __shared__ uint32_t base[64];
   __shared__ uint32_t wcnt[kSortWarps][64];
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
@@ -197,19 +236,19 @@ k_sort_large(int32_t n, const uint32_t* __restrict__ row_ptr, const uint32_t* __
     for (int i = threadIdx.x; i < 64; i += blockDim.x) base[i] = 0;
     for (int i = threadIdx.x; i < kSortWarps * 64; i += blockDim.x) (&wcnt[0][0])[i] = 0;
     __syncthreads();
-    for (uint32_t e = rb + threadIdx.x; e < re; e += blockDim.x) atomicAdd(&base[in[e] >> kNodeBits], 1u);
+    for (uint32_t e = rb + threadIdx.x; e < re; e += blockDim.x) atomicAdd(&base[(in[e] >> shift) & 63u], 1u);
     __syncthreads();
     if (threadIdx.x == 0) {
       uint32_t s = 0, top = 0;
       for (int b = 0; b < 64; ++b) { const uint32_t c = base[b]; base[b] = s; s += c; if (c) top = b; }
-      amax[u] = uint8_t(top);
+      if (amax) amax[u] = uint8_t(top);
     }
     __syncthreads();
     for (uint32_t c0 = rb; c0 < re; c0 += blockDim.x) {
       const uint32_t e = c0 + threadIdx.x;
       const bool valid = e < re;
       const uint32_t x = valid ? in[e] : 0u;
-      const uint32_t b = x >> kNodeBits;
+      const uint32_t b = (x >> shift) & 63u;
       const unsigned act = __ballot_sync(0xffffffffu, valid);
       uint32_t r = 0;
       if (valid) {
@@ -263,6 +302,22 @@ int grid_for(int64_t work, int threads) {
   const int64_t cap = int64_t(num_sms()) * 16;
   const int64_t g = (work + threads - 1) / threads;
   return int(std::max<int64_t>(1, std::min(g, cap)));
+}
+
+// Sort every row of `b` by its packed value, (level, neighbour): rows of more
+// than 32 entries by six stable digit passes through `a` and back, the short
+// rows in place; amax (if given) receives each row's largest level.
+void sort_rows(int32_t n, const uint32_t* d_row, uint32_t* a, uint32_t* b, uint8_t* amax) {
+  const int T = 256;
+  const uint32_t shifts[6] = {0, 6, 12, 18, 24, kNodeBits};
+  uint32_t* src = b;
+  uint32_t* dst = a;
+  for (int i = 0; i < 6; ++i) {
+    k_sort_pass<<<num_sms() * 8, kSortWarps * 32>>>(n, d_row, src, dst, shifts[i], i == 5 ? amax : nullptr);
+    std::swap(src, dst);
+  }
+  // six passes: the long rows are back in b
+  k_sort_small<<<grid_for(int64_t(n) * 32, T), T>>>(n, d_row, b, b, amax);
 }
 
 // Host: level of each count (Eq. 1-3, round half up), evaluated as printed:
@@ -331,22 +386,50 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
   const uint32_t m2 = uint32_t(d->m2);
   const int T = 256;
   int rc = RPQ_OK;
-  uint32_t *d_row = nullptr, *d_dl = nullptr, *d_cnt = nullptr, *d_scal = nullptr;
+  uint32_t *d_row = nullptr, *d_dl = nullptr, *d_cnt = nullptr, *d_scal = nullptr, *d_newrow = nullptr;
   int32_t* d_col = nullptr;
   uint16_t* d_lab = nullptr;
   uint8_t *d_amax = nullptr, *d_present = nullptr, *d_table = nullptr;
-  std::vector<uint32_t> row32(size_t(n) + 1);
+  std::vector<uint32_t>& row32 = kg->row_ext;
+  row32.resize(size_t(n) + 1);
   for (int64_t i = 0; i <= n; ++i) row32[i] = uint32_t(d->row_ptr[i]);
+  // internal numbering: decreasing degree, ties by caller id (counting sort)
+  std::vector<int32_t>& ext_of = kg->ext_of;
+  std::vector<int32_t>& int_of = kg->int_of;
+  ext_of.resize(size_t(n));
+  int_of.resize(size_t(n));
+  std::vector<uint32_t> new_row32(size_t(n) + 1, 0);
+  {
+    uint32_t maxd = 0;
+    for (int64_t v = 0; v < n; ++v) maxd = std::max(maxd, row32[v + 1] - row32[v]);
+    std::vector<int64_t> start(size_t(maxd) + 2, 0);
+    for (int64_t v = 0; v < n; ++v) ++start[maxd - (row32[v + 1] - row32[v]) + 1];
+    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+    for (int64_t v = 0; v < n; ++v) {
+      const int64_t id = start[maxd - (row32[v + 1] - row32[v])]++;
+      ext_of[size_t(id)] = int32_t(v);
+      int_of[size_t(v)] = int32_t(id);
+    }
+    for (int64_t i = 0; i < n; ++i)
+      new_row32[i + 1] = new_row32[i] + (row32[ext_of[i] + 1] - row32[ext_of[i]]);
+  }
   int64_t bytes = 0;
   auto cleanup = [&]() {
     cudaFree(d_dl); cudaFree(d_scal); cudaFree(d_col); cudaFree(d_lab); cudaFree(d_present); cudaFree(d_table);
+    cudaFree(d_row);
     kg->device_bytes += bytes;
   };
 #define TRY(x) do { rc = (x); if (rc != RPQ_OK) { cleanup(); return rc; } } while (0)
 #define TRYC(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) { \
     set_error(RPQ_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); cleanup(); return RPQ_ECUDA; } } while (0)
-  TRY(alloc_device((void**)&d_row, sizeof(uint32_t) * (size_t(n) + 1), &bytes));
-  kg->d_row_ptr = d_row;
+  TRY(alloc_device((void**)&d_row, sizeof(uint32_t) * (size_t(n) + 1), nullptr));   // caller row offsets
+  TRY(alloc_device((void**)&d_newrow, sizeof(uint32_t) * (size_t(n) + 1), &bytes));
+  kg->d_row_ptr = d_newrow;
+  TRY(alloc_device((void**)&kg->d_ext_of, sizeof(int32_t) * size_t(std::max(n, 1)), &bytes));
+  TRY(alloc_device((void**)&kg->d_int_of, sizeof(int32_t) * size_t(std::max(n, 1)), &bytes));
+  TRYC(cudaMemcpy(d_newrow, new_row32.data(), sizeof(uint32_t) * (size_t(n) + 1), cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(kg->d_ext_of, ext_of.data(), sizeof(int32_t) * size_t(n), cudaMemcpyHostToDevice));
+  TRYC(cudaMemcpy(kg->d_int_of, int_of.data(), sizeof(int32_t) * size_t(n), cudaMemcpyHostToDevice));
   TRY(alloc_device((void**)&d_amax, size_t(n), &bytes));
   kg->d_amax = d_amax;
   TRY(alloc_device((void**)&kg->d_lvx, sizeof(uint16_t) * kLvxLevels * size_t(n), &bytes));
@@ -399,26 +482,26 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
     TRYC(cudaMemcpy(d_table, table.data(), ncnt, cudaMemcpyHostToDevice));
     k_pack<<<grid_for(m2, T), T>>>(m2, d_cnt, d_col, d_table, cmin, ncnt);
     uint32_t* d_sorted = reinterpret_cast<uint32_t*>(d_col);  // the old col buffer becomes adj
-    k_sort_small<<<grid_for(int64_t(n) * 32, T), T>>>(n, d_row, d_cnt, d_sorted, d_amax);
-    k_sort_large<<<num_sms() * 8, kSortWarps * 32>>>(n, d_row, d_cnt, d_sorted, d_amax);
+    k_relabel<<<grid_for(m2, T), T>>>(n, m2, d_row, d_newrow, kg->d_int_of, d_cnt, d_sorted);
+    sort_rows(n, d_newrow, d_cnt, d_sorted, d_amax);
     TRYC(cudaGetLastError());
     TRYC(cudaDeviceSynchronize());
     kg->d_adj = d_sorted;  // same size as d_cnt, which it replaces
     d_col = nullptr;
     cudaFree(d_cnt);
   }
-  k_level_index<<<grid_for(n, T), T>>>(n, d_row, kg->d_adj, kg->d_lvx);
+  k_level_index<<<grid_for(n, T), T>>>(n, d_newrow, kg->d_adj, kg->d_lvx);
   {
     std::vector<uint32_t> long_rows;                   // fewer than 2^16: each holds > 2^16 of m2 < 2^32 entries
     for (int64_t v = 0; v < n; ++v)
-      if (row32[v + 1] - row32[v] > kLvxMaxDeg) long_rows.push_back(uint32_t(v));
+      if (new_row32[v + 1] - new_row32[v] > kLvxMaxDeg) long_rows.push_back(uint32_t(v));
     const uint32_t n_long = uint32_t(long_rows.size());
     TRY(alloc_device((void**)&kg->d_lvx_long, sizeof(uint32_t) * kLvxLevels * size_t(n_long), &bytes));
     if (n_long) {
       // d_dl (m2 entries, no longer needed) holds the list of long rows
       TRYC(cudaMemcpy(d_dl, long_rows.data(), sizeof(uint32_t) * n_long, cudaMemcpyHostToDevice));
       const uint32_t tasks = n_long * kLvxLevels;
-      k_level_index_long<<<(tasks + T - 1) / T, T>>>(n, n_long, d_dl, d_row, kg->d_adj, kg->d_lvx, kg->d_lvx_long);
+      k_level_index_long<<<(tasks + T - 1) / T, T>>>(n, n_long, d_dl, d_newrow, kg->d_adj, kg->d_lvx, kg->d_lvx_long);
     }
   }
   TRYC(cudaGetLastError());
@@ -427,6 +510,39 @@ int build_graph(rpq_kg* kg, const rpq_kg_desc* d) {
   return RPQ_OK;
 #undef TRY
 #undef TRYC
+}
+
+// The packed adjacency and amax in the caller's numbering: rows in caller
+// order, each sorted by (level, caller neighbour id).
+int export_graph(const rpq_kg* kg, uint32_t* adj, uint8_t* amax) {
+  const int32_t n = kg->dev.n;
+  const uint32_t m2 = uint32_t(kg->m2);
+  if (adj && m2) {
+    uint32_t *a = nullptr, *b = nullptr, *row = nullptr;
+    int rc = alloc_device((void**)&a, sizeof(uint32_t) * size_t(m2), nullptr);
+    if (rc == RPQ_OK) rc = alloc_device((void**)&b, sizeof(uint32_t) * size_t(m2), nullptr);
+    if (rc == RPQ_OK) rc = alloc_device((void**)&row, sizeof(uint32_t) * (size_t(n) + 1), nullptr);
+    cudaError_t e = cudaSuccess;
+    if (rc == RPQ_OK) {
+      const int T = 256;
+      e = cudaMemcpy(row, kg->row_ext.data(), sizeof(uint32_t) * (size_t(n) + 1), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) {
+        k_relabel<<<grid_for(m2, T), T>>>(n, m2, kg->d_row_ptr, row, kg->d_ext_of, kg->d_adj, b);
+        sort_rows(n, row, a, b, nullptr);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaMemcpy(adj, b, sizeof(uint32_t) * size_t(m2), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) { set_error(RPQ_ECUDA, "export: %s", cudaGetErrorString(e)); rc = RPQ_ECUDA; }
+    }
+    cudaFree(a); cudaFree(b); cudaFree(row);
+    if (rc != RPQ_OK) return rc;
+  }
+  if (amax && n > 0) {
+    std::vector<uint8_t> in(static_cast<size_t>(n));
+    RPQ_CUDA(cudaMemcpy(in.data(), kg->d_amax, size_t(n), cudaMemcpyDeviceToHost));
+    for (int64_t u = 0; u < n; ++u) amax[u] = in[size_t(kg->int_of[size_t(u)])];
+  }
+  return RPQ_OK;
 }
 
 }  // namespace rpq

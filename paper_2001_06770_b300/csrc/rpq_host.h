@@ -108,7 +108,11 @@ struct rpq_kg {
   uint16_t* d_lvx = nullptr;
   uint32_t* d_lvx_long = nullptr;
   uint32_t* d_kw_ptr = nullptr;
-  int32_t* d_kw_nodes = nullptr;
+  int32_t* d_kw_nodes = nullptr;        // postings in internal ids
+  int32_t* d_ext_of = nullptr;          // internal -> caller node id
+  int32_t* d_int_of = nullptr;          // caller -> internal node id
+  std::vector<int32_t> ext_of, int_of;  // host copies
+  std::vector<uint32_t> row_ext;        // caller row offsets (for exports)
   int64_t device_bytes = 0;
   std::vector<int64_t> kw_ptr;   // host copy of the postings offsets
   std::vector<rpq::Slot*> slots; // search slots, created on first use
@@ -120,6 +124,8 @@ struct rpq_kg {
 namespace rpq {
 // Fill d_row_ptr, d_adj and d_amax of kg from the host CSR (kg_build.cu).
 int build_graph(rpq_kg* kg, const rpq_kg_desc* d);
+// The packed adjacency and amax in caller ids (kg_build.cu).
+int export_graph(const rpq_kg* kg, uint32_t* adj, uint8_t* amax);
 
 // Search slots and query execution (api.cu).
 int create_slot(rpq_kg* kg, Slot** out, bool own_cols = true);

@@ -17,7 +17,9 @@
 //   stopl    uint8[n]      level at which the cf bit was set
 //   items    Item[n]       expansion work list of the current level (8 B each,
 //                          column masks in imask uint16[n])
-//   cg       uint32[n]     identified CGs, (level << 26) | node
+//   cg       uint32[n]     identified CGs, (level << 26) | caller node id
+// Node ids inside the device structures are internal (decreasing degree, see
+// kg_build.cu); CG keys, selected CGs and results carry the caller's ids.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -65,7 +67,9 @@ struct DevKG {
   const uint32_t* lvx_long;   // kLvxLevels per row longer than kLvxMaxDeg
   int32_t n_kw;
   const uint32_t* kw_ptr;
-  const int32_t* kw_nodes;
+  const int32_t* kw_nodes;    // internal ids
+  const int32_t* ext_of;      // internal -> caller node id
+  const int32_t* int_of;      // caller -> internal node id
 };
 
 // One expansion work item: the newly active segment of a frontier node.  The
@@ -97,6 +101,8 @@ struct QueryDev {
 struct Ctl {
   unsigned long long work[2];  // per level parity: (items << 38) | work units
   uint32_t done;               // current run finished
+  uint32_t exp_skip;           // the run had finished before this level's enqueue: its expansion exits
+                               // at once (every block of the launch that stops the run still runs)
   uint32_t level;              // last identified level of the current run
   int32_t last_expanded;       // last level with an expansion (-1: none)
   uint32_t nq[2];              // |Q_l| per level parity
@@ -128,7 +134,8 @@ struct Ctl {
   unsigned long long seeded[2]; // (node, column) pairs seeded with h = 0
   unsigned long long units, items, frontier;  // work totals of both runs
   int32_t levels[2];           // last identified level per run
-  int32_t sel[kMaxK];
+  int32_t sel[kMaxK];          // selected CGs, caller ids (ranking ties by caller id)
+  int32_t sel_int[kMaxK];      // the same nodes, internal ids
   uint8_t sel_sc[kMaxK];
   uint8_t matched[kMaxK];
   uint8_t sm[kMaxK];

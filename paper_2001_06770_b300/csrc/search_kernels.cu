@@ -90,9 +90,12 @@ __device__ __forceinline__ void vis_or(uint32_t* vis, uint32_t v, uint32_t bits)
 // ------------------------------------------------------------ query set-up
 __global__ void k_set_query(DevSlot s, QueryDev qv, const int32_t* d_kw) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  QueryDev q = qv;
-  if (d_kw) for (int i = 0; i < q.n_c + q.n_m; ++i) q.kw[i] = d_kw[i];
-  *s.q = q;
+  // the record goes to global memory first and the keyword ids are patched
+  // there (with nvcc 13.0 for sm_103a, a modified local copy of the by-value
+  // record stored back lost the patched ids)
+  QueryDev* dst = s.q;
+  *dst = qv;
+  if (d_kw) for (int i = 0; i < qv.n_c + qv.n_m; ++i) dst->kw[i] = d_kw[i];
   Ctl* c = s.ctl;
   uint32_t* w = reinterpret_cast<uint32_t*>(c);
   for (size_t i = 0; i < sizeof(Ctl) / 4; ++i) w[i] = 0;
@@ -246,11 +249,13 @@ __device__ bool theorem4_stop(const Ctl* c, const uint8_t* matched, const uint8_
 // Items are compacted with warp ballots, a block scan and one 64-bit
 // atomicAdd per block tile; each item also marks the warp tiles of the
 // expansion that start inside it.
-template <bool P>
+// NT is the run's number of keyword columns (1..kMaxCols), a compile-time
+// constant so that the per-node column loops hold exactly the run's columns.
+template <bool P, int NT>
 __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
-  const int nt = run == 0 ? q.n_c : q.n_m;
+  constexpr int nt = NT;
   const uint32_t full = (1u << nt) - 1u;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   constexpr uint32_t nwarp = kEnqThreads / 32;
@@ -352,27 +357,27 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       uint8_t eq = 0, lt = 0;
       // every load of the node first (they are independent), then the logic
       uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
-      uint32_t hv[kMaxCols];
+      uint32_t hv[nt];
       if (has && ident_only) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) hv[j] = l;   // a node completed at this level has max h = l
+        for (int j = 0; j < nt; ++j) hv[j] = l;         // a node completed at this level has max h = l
       } else if (has) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
         rb = g.row_ptr[v];
         re = g.row_ptr[v + 1];
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) hv[j] = j < nt ? ldx<P>(hcol(q, j) + v) : 0u;
+        for (int j = 0; j < nt; ++j) hv[j] = ldx<P>(hcol(q, j) + v);
         if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
         if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
       }
       if (has && !((cfw >> (v & 31u)) & 1u)) {
         uint32_t mx = 0;
 #pragma unroll
-        for (int j = 0; j < kMaxCols; ++j) {
-          if (j >= nt || !((vb >> j) & 1u)) continue;
+        for (int j = 0; j < nt; ++j) {
+          if (!((vb >> j) & 1u)) continue;
           const uint32_t h = hv[j];
           mx = h > mx ? h : mx;
           if (h == l) eq |= uint8_t(1u << j);
@@ -383,7 +388,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
           stop_now = true;
           if (run == 0) {
             is_cg = true;
-            cg_key = (mx << kNodeBits) | v;
+            cg_key = (mx << kNodeBits) | uint32_t(g.ext_of[v]);   // ranked by (S^c, caller id)
             if (mx != l) atomicOr(&c->err, kErrInternal);
           }
         } else {
@@ -477,13 +482,31 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   if (threadIdx.x == 0 && et) atomicAdd(&c->eact_lvl[p], (unsigned long long)et);
 }
 
+// The enqueue of the run's column count (the same in every thread).
+template <bool P>
+__device__ __forceinline__ void enqueue_columns(const DevKG& g, const DevSlot& s, int run, uint32_t l) {
+  const QueryDev& q = *s.q;
+  switch (run == 0 ? q.n_c : q.n_m) {
+    case 1: enqueue_level<P, 1>(g, s, run, l); break;
+    case 2: enqueue_level<P, 2>(g, s, run, l); break;
+    case 3: enqueue_level<P, 3>(g, s, run, l); break;
+    case 4: enqueue_level<P, 4>(g, s, run, l); break;
+    case 5: enqueue_level<P, 5>(g, s, run, l); break;
+    case 6: enqueue_level<P, 6>(g, s, run, l); break;
+    case 7: enqueue_level<P, 7>(g, s, run, l); break;
+    default: enqueue_level<P, kMaxCols>(g, s, run, l); break;
+  }
+}
+
 __global__ void __launch_bounds__(kEnqThreads, 5)      // at most 51 registers: 5 blocks per SM
 k_enqueue(DevKG g, DevSlot s, int run) {
   Ctl* c = s.ctl;
-  if (c->done) return;
+  const bool done = c->done != 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->exp_skip = done ? 1u : 0u;   // read by this level's k_expand
+  if (done) return;
   const uint32_t l = c->lvl_enq;
   if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
-  enqueue_level<false>(g, s, run, l);
+  enqueue_columns<false>(g, s, run, l);
 }
 
 // ------------------------------------------- level: V_C check (marginal run)
@@ -809,7 +832,10 @@ __global__ void __launch_bounds__(kExpThreads)
 k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
   Ctl* c = s.ctl;
   if (blockIdx.x == 0 && threadIdx.x == 0) c->iters[run] += 1;
-  if (c->done) {
+  // exp_skip, not done: block 0 of the launch that stops the run sets done
+  // while other blocks of that launch may still be starting, and they too
+  // must take the stop path (their share of the hit count)
+  if (c->exp_skip) {
     if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
     return;
   }
@@ -855,7 +881,7 @@ k_run(DevKG g, DevSlot s, int run) {
   for (;;) {
     const uint32_t l = *(volatile uint32_t*)&c->lvl_enq;
     if (blockIdx.x == 0 && threadIdx.x == 0) { c->lvl_exp = l; c->iters[run] += 1; }
-    enqueue_level<true>(g, s, run, l);
+    enqueue_columns<true>(g, s, run, l);
     if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
     if (expand_level<true>(g, s, run, l, 0, 0)) return;
     if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
@@ -964,7 +990,7 @@ __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K
   return min(valid, K);
 }
 
-__global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
+__global__ void __launch_bounds__(kTopkThreads) k_topk(DevKG g, DevSlot s) {
   Ctl* c = s.ctl;
   const uint32_t K = uint32_t(s.q->w);                   // beam width w
   const uint32_t n_in = min(c->ncg, s.cap);
@@ -1023,11 +1049,14 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevSlot s) {
     s_sel[rank] = v;
   }
   __syncthreads();
+  if (threadIdx.x < total) {
+    const int32_t ext = int32_t(s_sel[threadIdx.x] & kNodeMask);
+    c->sel[threadIdx.x] = ext;
+    c->sel_int[threadIdx.x] = g.int_of[ext];
+    c->sel_sc[threadIdx.x] = uint8_t(s_sel[threadIdx.x] >> kNodeBits);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    for (uint32_t i = 0; i < total; ++i) {
-      c->sel[i] = int32_t(s_sel[i] & kNodeMask);
-      c->sel_sc[i] = uint8_t(s_sel[i] >> kNodeBits);
-    }
     c->nsel = total;
     c->ulist_n = 0;
     c->nvc = 0;
@@ -1102,7 +1131,7 @@ k_recover_cols(DevKG g, DevSlot s) {
   };
   if (rank == 0) {
     for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
-      const uint32_t v = uint32_t(c->sel[gi]);
+      const uint32_t v = uint32_t(c->sel_int[gi]);
       if (j == 0) {                                  // the CG nodes themselves belong to V^c
         const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
         if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
@@ -1366,7 +1395,7 @@ void launch_level(const DevKG& g, const DevSlot& s, int run, cudaStream_t st, Pr
 void launch_select_recover(const DevKG& g, const DevSlot& s, int n_m, cudaStream_t st, Prof* prof) {
   const int sms = num_sms();
   timed(prof, RPQ_PROF_TOPK, st, [&] {
-    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(s);
+    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(g, s);
   });
   if (n_m > 0) {
     timed(prof, RPQ_PROF_RECOVER, st, [&] {
@@ -1415,7 +1444,7 @@ int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st
   for (int l = 0; l <= L; ++l) launch_level(g, s, 0, st, prof, 0, false);
   const int sms = num_sms();
   timed(prof, RPQ_PROF_TOPK, st, [&] {
-    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(s);
+    k_topk<<<sms * 2, kTopkThreads, 0, st>>>(g, s);
   });
   return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kSwThreads) k_sg_sweep(DevKG g, DevSlot s, int
   const int maxlev = c->levels[run];
   if (run == 0) {
     for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x)
-      sweep_seed(s, rmask, rlist, &s_n, uint32_t(c->sel[gi]), 1ull << gi);
+      sweep_seed(s, rmask, rlist, &s_n, uint32_t(c->sel_int[gi]), 1ull << gi);
   } else {
     const uint32_t nvc = min(c->nvc, s.cap);
     for (uint32_t i = threadIdx.x; i < nvc; i += blockDim.x) {     // d_j(g) = min over V_C(g)
@@ -703,5 +703,8 @@ extern "C" int rpq_search_subgraphs(rpq_kg* kg, const rpq_query* q, rpq_result* 
     RPQ_CUDA(cudaMemcpy(sgo->nodes, x->d.nodes, sizeof(uint32_t) * nodes_total, cudaMemcpyDeviceToHost));
   if (edges_total)
     RPQ_CUDA(cudaMemcpy(sgo->edges, x->d.edges, sizeof(uint2) * edges_total, cudaMemcpyDeviceToHost));
+  // the lists hold internal ids: give them back in the caller's ids
+  for (uint64_t i = 0; i < nodes_total; ++i) sgo->nodes[i] = kg->ext_of[size_t(sgo->nodes[i])];
+  for (uint64_t i = 0; i < 2 * edges_total; ++i) sgo->edges[i] = kg->ext_of[size_t(sgo->edges[i])];
   return RPQ_OK;
 }
