@@ -127,6 +127,20 @@ __global__ void k_run_start(DevSlot s, int run) {
   c->last_expanded = -1;
 }
 
+// Position of the n-th (0-based) set bit of w; n < popc(w).
+__device__ __forceinline__ uint32_t nth_set_bit(uint32_t w, uint32_t n) {
+  uint32_t pos = 0, c = __popc(w & 0xffffu);
+  if (n >= c) { n -= c; w >>= 16; pos += 16; }
+  c = __popc(w & 0xffu);
+  if (n >= c) { n -= c; w >>= 8; pos += 8; }
+  c = __popc(w & 0xfu);
+  if (n >= c) { n -= c; w >>= 4; pos += 4; }
+  c = __popc(w & 0x3u);
+  if (n >= c) { n -= c; w >>= 2; pos += 2; }
+  if (n >= (w & 1u)) pos += 1;
+  return pos;
+}
+
 // Append the flagged lanes' nodes to frontier queue p (warp aggregated).  The
 // queue is abandoned (flag set) once it would exceed its limit; the bitmap F
 // stays complete either way.
@@ -319,32 +333,54 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   uint64_t eact = 0;                                   // E_act of this level (Algorithm 1's activations)
   for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
     uint32_t it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
-    // candidate node of each round: bitmap mode, word tile/32 + r*nwarp + warp
-    // with lane = bit; queue mode, entry tile + r*blockDim + threadIdx
+    // Candidate node of each round.  Queue mode: entry tile + threadIdx, one
+    // round.  Bit-map mode: the warp owns words w0 .. w0 + kEnqRounds - 1 of
+    // F_l and packs their set bits onto its lanes, the k-th frontier node of
+    // the warp going to round k / 32, lane k % 32: a warp runs one round per
+    // 32 frontier nodes instead of one per word, so on a level where a few
+    // bits in ten are set most rounds are not run at all.
+    constexpr uint32_t kNone = 0xffffffffu;            // no node in this round and lane
     uint32_t cand[kEnqRounds];
-    bool has_r[kEnqRounds];
+    uint32_t total = 0;                                // the warp's frontier nodes (bit-map mode)
+    const uint32_t w0 = tile / 32u + warp * kEnqRounds;
+    if (sparse) {
+      const uint32_t i = tile + threadIdx.x;
+      cand[0] = i < nsrc ? ldx<P>(s.fq[p] + i) : kNone;
 #pragma unroll
-    for (int r = 0; r < kEnqRounds; ++r) {
-      if (sparse) {
-        const uint32_t i = tile + threadIdx.x;
-        has_r[r] = r == 0 && i < nsrc;
-        cand[r] = has_r[r] ? ldx<P>(s.fq[p] + i) : 0u;
-      } else {
-        const uint32_t widx = tile / 32u + r * nwarp + warp;
-        const uint32_t word = widx < nwords ? ldx<P>(Fc + widx) : 0u;
-        has_r[r] = (word >> lane) & 1u;
-        cand[r] = widx * 32u + lane;
-        if (lane == 0 && word) Fc[widx] = 0;           // reset F for its next use
+      for (int r = 1; r < kEnqRounds; ++r) cand[r] = kNone;
+    } else {
+      uint32_t wd[kEnqRounds], wpre[kEnqRounds + 1];   // the warp's words and their prefix counts
+      wpre[0] = 0;
+#pragma unroll
+      for (int r = 0; r < kEnqRounds; ++r) {
+        wd[r] = w0 + r < nwords ? ldx<P>(Fc + w0 + r) : 0u;
+        wpre[r + 1] = wpre[r] + __popc(wd[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < kEnqRounds; ++r)
+        if (lane == uint32_t(r) && wd[r]) Fc[w0 + r] = 0;   // reset F for its next use
+      total = wpre[kEnqRounds];
+#pragma unroll
+      for (int r = 0; r < kEnqRounds; ++r) {
+        const uint32_t k = uint32_t(r) * 32u + lane;
+        uint32_t word = wd[0], base = 0, ww = 0;
+#pragma unroll
+        for (int x = 1; x < kEnqRounds; ++x)
+          if (k >= wpre[x]) { word = wd[x]; base = wpre[x]; ww = uint32_t(x); }
+        cand[r] = k < total ? (w0 + ww) * 32u + nth_set_bit(word, k - base) : kNone;
       }
     }
+    // rounds this warp runs (the same in every lane)
+    const uint32_t nr = sparse ? 1u : (total + 31u) >> 5;
     uint32_t my_items = 0, my_work = 0;
 #pragma unroll
     for (int r = 0; r < kEnqRounds; ++r) {
       it_len[r] = 0;
       it_seg[r] = 0; it_msk[r] = 0;
-      const bool has = has_r[r];
+      if (uint32_t(r) >= nr) continue;                 // the same in every lane
+      const bool has = cand[r] != kNone;
       if (!__any_sync(0xffffffffu, has)) continue;
-      const uint32_t v = cand[r];
+      const uint32_t v = has ? cand[r] : 0u;
       if (sparse && has) Fc[v >> 5] = 0;               // every set bit of F_l is in the queue
       qcount += has;
       if (s.qlog && has) {
@@ -424,11 +460,17 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       if (sparse) {                                     // nodes of a warp lie in different words
         if (stop_now) atomicOr(s.cf + (v >> 5), 1u << (v & 31u));
         if (retain) atomicOr(Fn + (v >> 5), 1u << (v & 31u));
-      } else {                                          // the warp owns word v >> 5: one update each
-        const unsigned sb = __ballot_sync(0xffffffffu, stop_now);
-        const unsigned rb = __ballot_sync(0xffffffffu, retain);
-        if (lane == 0 && sb) atomicOr(s.cf + (v >> 5), sb);
-        if (lane == 0 && rb) atomicOr(Fn + (v >> 5), rb);   // F_{l+1} is empty before this level
+      } else {                                          // the warp owns words w0..: one update each
+        // this round's nodes lie in the words of its first and last lanes with a node
+        const uint32_t bit = 1u << (v & 31u), mw = v >> 5;
+        const uint32_t last = min(31u, total - 1u - uint32_t(r) * 32u);
+        const uint32_t wf = __shfl_sync(0xffffffffu, mw, 0), wl = __shfl_sync(0xffffffffu, mw, last);
+        for (uint32_t x = wf; x <= wl; ++x) {
+          const uint32_t sb = __reduce_or_sync(0xffffffffu, (stop_now && mw == x) ? bit : 0u);
+          const uint32_t rbm = __reduce_or_sync(0xffffffffu, (retain && mw == x) ? bit : 0u);
+          if (lane == 0 && sb) atomicOr(s.cf + x, sb);
+          if (lane == 0 && rbm) atomicOr(Fn + x, rbm);   // F_{l+1} is empty before this level
+        }
       }
       queue_push(s, c, p ^ 1, sparse, retain, v);
     }
@@ -443,6 +485,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       uint32_t off = uint32_t((s_base & kWorkMask) + (pre & kWorkMask));
 #pragma unroll
       for (int r = 0; r < kEnqRounds; ++r) {           // every lane runs every round (warp-wide fill)
+        if (uint32_t(r) >= nr) break;                  // the same in every lane
         const bool has = it_len[r] != 0;
         uint32_t t0 = 1, t1 = 0;                       // warp tiles starting inside the item
         if (has) {
