@@ -51,10 +51,11 @@ WORKLOAD_LARGE = ("large: Chung-Lu (exponent 2.1) 5e7 nodes, 4e8 sampled edges, 
 REL_TOL = 1e-6   # S^r; node ids, S^c and S^m must be equal
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6400.0
-# DRAM bytes per expansion launch from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the kernel source with this SHA-1 prefix; the
-# value is reported only while the kernel source is unchanged.
-NCU_TRAFFIC = {"sha1": "9e025e4dbd13", "bytes_per_launch": 5063236}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)
+# of every expansion launch of a workload's first queries, per workload, for
+# the kernel source with this SHA-1 prefix; reported only while the
+# expansion source is unchanged.
+NCU_TRAFFIC = {}
 
 
 def expand_source_sha() -> str:
@@ -328,10 +329,11 @@ def expand_roofline(kg, qs, stats, workload="medium"):
     kg.set_profiling(True)
     kg.profile(reset=True)
     kg.profile_levels(reset=True)
-    for q in qs:
+    recs = []
+    for i, q in enumerate(qs):
         kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
+        recs += [dict(r, query=i) for r in kg.profile_levels(reset=True)]
     prof = kg.profile(reset=True)
-    recs = kg.profile_levels(reset=True)
     kg.set_profiling(False)
     peak, peak_kind = hbm_peak()
     exp_ms, exp_launches = prof["expand"]
@@ -348,12 +350,23 @@ def expand_roofline(kg, qs, stats, workload="medium"):
     dense = [r for r in expanded if r["units"] >= DENSE_UNITS]
     e_all, e_dense, q_all = agg(expanded, "expand"), agg(dense, "expand"), agg(recs, "enqueue")
     q_dense = agg([r for r in recs if r["frontier"] >= (1 << 18)], "enqueue")
-    traffic = (NCU_TRAFFIC["bytes_per_launch"]
-               if workload == "medium" and len(qs) == 64 and NCU_TRAFFIC["sha1"] == expand_source_sha() else None)
-    avg_s = e_all["ms"] / 1e3 / max(e_all["launches"], 1)
-    dram_gbs = traffic / avg_s / 1e9 if traffic and avg_s > 0 else None
+    # DRAM bytes of the expansion launches of the workload's first queries,
+    # from one ncu capture of the same kernel source (NCU_TRAFFIC), beside the
+    # algorithmic bytes and device time of the same launches in this pass
+    cap = NCU_TRAFFIC.get(workload)
+    traffic = dram_gbs = traffic_ratio = None
+    if cap and cap["sha1"] == expand_source_sha() and len(qs) >= cap["queries"]:
+        same = [r for r in expanded if r["query"] < cap["queries"]]
+        if len(same) == cap["launches"]:
+            a = agg(same, "expand")
+            traffic = cap["dram_bytes"] / cap["launches"]
+            traffic_ratio = cap["dram_bytes"] / a["alg_bytes"] if a["alg_bytes"] else None
+            dram_gbs = cap["dram_bytes"] / (a["ms"] / 1e3) / 1e9 if a["ms"] > 0 else None
     roof = {"bound": "hbm", "kernel": "k_expand", "achieved": e_all["achieved"], "peak": peak, "unit": "GB/s",
             "frac": e_all["frac"], "traffic": traffic, "peak_kind": peak_kind,
+            "traffic_note": (f"ncu DRAM bytes per launch over the expansion launches of the first "
+                             f"{cap['queries']} queries" if traffic else None),
+            "traffic_over_alg_bytes": traffic_ratio,
             "dram_gbs": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
             "alg_bytes_per_launch": e_all["alg_bytes_per_launch"], "avg_launch_us": e_all["avg_launch_us"],
             "launches": e_all["launches"], "share_of_device_time": exp_ms / total_ms if total_ms else None,

@@ -109,7 +109,7 @@ static std::vector<std::pair<void**, size_t>> slot_arrays(const rpq_kg* kg, DevS
   d.tgt_cap = d.cap;
   size_t vb = 0, fb = 0;
   run_clear_layout(n, &vb, &fb);
-  d.run_clear_bytes = vb + 3 * fb;             // visited bytes, F[0], F[1], cf
+  d.run_clear_bytes = 2 * vb + 3 * fb;         // visited bytes, seen bytes, F[0], F[1], cf
   std::vector<std::pair<void**, size_t>> v = {
       {&d.run_clear, d.run_clear_bytes},
       {(void**)&d.stopl, n + 16},
@@ -169,9 +169,10 @@ int create_slot(rpq_kg* kg, Slot** out, bool own_cols) {
     size_t vb = 0, fb = 0;
     run_clear_layout(size_t(kg->dev.n), &vb, &fb);
     d.vis = reinterpret_cast<uint32_t*>(b);
-    d.F[0] = reinterpret_cast<uint32_t*>(b + vb);
-    d.F[1] = reinterpret_cast<uint32_t*>(b + vb + fb);
-    d.cf = reinterpret_cast<uint32_t*>(b + vb + 2 * fb);
+    d.vseen = reinterpret_cast<uint8_t*>(b + vb);
+    d.F[0] = reinterpret_cast<uint32_t*>(b + 2 * vb);
+    d.F[1] = reinterpret_cast<uint32_t*>(b + 2 * vb + fb);
+    d.cf = reinterpret_cast<uint32_t*>(b + 2 * vb + 2 * fb);
     d.res = reinterpret_cast<char*>(d.ctl) + kCtlBytes;   // one copy returns control block and results
     // masks start at zero; the recovery kernel restores zero after each use
     if ((own_cols && cudaMemset(d.rmask, 0, sizeof(unsigned long long) * d.cap * kMaxCols) != cudaSuccess) ||

@@ -166,6 +166,7 @@ constexpr size_t kCtlBytes = (sizeof(Ctl) + 15) / 16 * 16;
 struct DevSlot {
   uint8_t* H;                 // the slot's own columns (kMaxCols * hp bytes), or NULL (server slots)
   uint32_t* vis;
+  uint8_t* vseen;             // per node: the visited bits the enqueue has written H for
   uint32_t* F[2];
   uint32_t* cf;
   uint8_t* stopl;

@@ -30,12 +30,15 @@
 // a, so they form one segment).  An edge with a smaller max was already
 // handled at that earlier level by the same node (which was in the frontier
 // then, because it is retained while it has an edge with a > level), so
-// skipping Algorithm 1's re-scan changes no h value.  Every thread that finds
-// a column of a neighbour unreached (its visited bit clear) at level l writes
-// h = l+1 there: the visited bits set before the launch are all visible, so
-// the column was not reached at an earlier level, and any other writer of
-// this launch stores the same l+1 (Theorem 6).  The visited and frontier
-// bits are then set with reductions that return nothing.
+// skipping Algorithm 1's re-scan changes no h value.  A thread that finds a
+// column of a neighbour unreached (its visited bit clear) at level l claims
+// it: it sets the visited and frontier bits with reductions that return
+// nothing.  The claimed column's level is l+1 whoever claims it (Theorem 6:
+// the bits set before the launch are all visible, so the column was not
+// reached at an earlier level), and the node is in F_{l+1}, so the enqueue
+// of level l+1 writes h = l+1 for every column that is new since it last
+// saw the node (its seen byte): the hit levels are written once, coalesced,
+// instead of as scattered bytes by every claim.
 #include <algorithm>
 #include <cstdio>
 
@@ -392,22 +395,36 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       uint32_t cg_key = 0;
       uint8_t eq = 0, lt = 0;
       // every load of the node first (they are independent), then the logic
-      uint32_t cfw = 0, vb = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
+      uint32_t cfw = 0, vb = 0, seen = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
       uint32_t hv[nt];
       if (has && ident_only) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
+        seen = ldx<P>(s.vseen + v);
 #pragma unroll
         for (int j = 0; j < nt; ++j) hv[j] = l;         // a node completed at this level has max h = l
       } else if (has) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
+        seen = ldx<P>(s.vseen + v);
         rb = g.row_ptr[v];
         re = g.row_ptr[v + 1];
 #pragma unroll
         for (int j = 0; j < nt; ++j) hv[j] = ldx<P>(hcol(q, j) + v);
         if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
         if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
+      }
+      // columns claimed since this node was last enqueued were reached at
+      // this level: their hit level is l, written here once
+      const uint32_t fresh = has ? (vb & ~seen & full) : 0u;
+      if (fresh) {
+#pragma unroll
+        for (int j = 0; j < nt; ++j) {
+          if (!((fresh >> j) & 1u)) continue;
+          hcol(q, j)[v] = uint8_t(l);
+          hv[j] = l;
+        }
+        s.vseen[v] = uint8_t(vb);
       }
       if (has && !((cfw >> (v & 31u)) & 1u)) {
         uint32_t mx = 0;
@@ -817,7 +834,9 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
     }
     uint32_t x_r[kExpRounds];
 #pragma unroll
-    for (int r = 0; r < kExpRounds; ++r) x_r[r] = v_r[r] ? __ldg(g.adj + e_r[r]) : 0u;
+    // the adjacency is streamed (each entry read once per level): evict-first,
+    // so that it does not push the visited and frontier lines out of L2
+    for (int r = 0; r < kExpRounds; ++r) x_r[r] = v_r[r] ? __ldcs(g.adj + e_r[r]) : 0u;
     uint32_t vb_r[kExpRounds];
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
@@ -832,8 +851,9 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       const uint32_t act = a < l ? eq : (eq | lt);   // columns for which the edge is new at level l
       nw_r[r] = act & ~vb_r[r];
     }
-    // Claims: h = l+1 for every column found unreached, then the visited and
-    // frontier bits by reductions.  A returning atomic only where its old
+    // Claims: the visited and frontier bits of every column found unreached,
+    // by reductions (the level l+1 is written by the next enqueue).  A
+    // returning atomic only where its old
     // value is used: when this claim may complete a central node (the count
     // lets the next enqueue skip its work items if the run stops there; a
     // completion whose claims all looked incomplete is not counted, which
@@ -845,7 +865,6 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       const uint32_t nb = x_r[r] & kNodeMask;
       const uint32_t nw = nw_r[r];
       if (nw) {
-        for (uint32_t m = nw; m; m &= m - 1) hcol(q, __ffs(m) - 1)[nb] = uint8_t(l + 1);
         const uint32_t sh = (nb & 3u) * 8u;
         if (((vb_r[r] | nw) & fullc) == fullc) {
           const uint32_t ob = (atomicOr(s.vis + (nb >> 2), nw << sh) >> sh) & 0xffu;
