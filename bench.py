@@ -55,7 +55,10 @@ FALLBACK_HBM = 6400.0
 # of every expansion launch of a workload's first queries, per workload, for
 # the kernel source with this SHA-1 prefix; reported only while the
 # expansion source is unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 8 queries of the large workload, one B300, every k_expand launch (80)
+    "large": {"sha1": "6ea25d34b7a6", "queries": 8, "launches": 80, "dram_bytes": 24113970944},
+}
 
 
 def expand_source_sha() -> str:
@@ -356,7 +359,7 @@ def expand_roofline(kg, qs, stats, workload="medium"):
     cap = NCU_TRAFFIC.get(workload)
     traffic = dram_gbs = traffic_ratio = None
     if cap and cap["sha1"] == expand_source_sha() and len(qs) >= cap["queries"]:
-        same = [r for r in expanded if r["query"] < cap["queries"]]
+        same = [r for r in recs if r["query"] < cap["queries"]]     # every k_expand launch of those queries
         if len(same) == cap["launches"]:
             a = agg(same, "expand")
             traffic = cap["dram_bytes"] / cap["launches"]
@@ -405,7 +408,7 @@ def run(args):
         qs = qs[:args.queries]
     kg = rpq.KG.from_dataset(ds)
     # work-split parameters picked by the library's autotuner on a sample
-    tuned = kg.autotune(qs[:args.tune_queries], repeats=2) if args.autotune else kg.tuning()
+    tuned = kg.autotune(qs[:args.tune_queries], repeats=3) if args.autotune else kg.tuning()
     args.tuning = tuned
     if wl["mode"] == "batch":
         line = run_batch(args, ws, rank, local, wl, ds, qs, kg)
@@ -709,7 +712,7 @@ def main():
                     help="large (default, the benchmark line), medium, batched or served")
     ap.add_argument("--queries", type=int, default=0, help="use only the first Q queries of the workload")
     ap.add_argument("--autotune", type=int, default=1, help="run the library's autotuner first (1) or not (0)")
-    ap.add_argument("--tune-queries", type=int, default=16, help="queries of the workload the autotuner times")
+    ap.add_argument("--tune-queries", type=int, default=32, help="queries of the workload the autotuner times")
     ap.add_argument("--profile-only", type=int, default=0, metavar="Q",
                     help="load the workload, run its first Q queries once through rpq_search and exit "
                          "(a short command for ncu captures); prints no JSON line")
