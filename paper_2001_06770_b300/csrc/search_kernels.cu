@@ -396,53 +396,42 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       uint8_t eq = 0, lt = 0;
       // every load of the node first (they are independent), then the logic
       uint32_t cfw = 0, vb = 0, seen = 0, rb = 0, re = 0, o_lo = 0, o_hi = 0;
-      uint32_t hv[nt];
-      if (has && ident_only) {
+      if (has) {
         cfw = ldx<P>(s.cf + (v >> 5));
         vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
         seen = ldx<P>(s.vseen + v);
-#pragma unroll
-        for (int j = 0; j < nt; ++j) hv[j] = l;         // a node completed at this level has max h = l
-      } else if (has) {
-        cfw = ldx<P>(s.cf + (v >> 5));
-        vb = ldx<P>(reinterpret_cast<const uint8_t*>(s.vis) + v);
-        seen = ldx<P>(s.vseen + v);
-        rb = g.row_ptr[v];
-        re = g.row_ptr[v + 1];
-#pragma unroll
-        for (int j = 0; j < nt; ++j) hv[j] = ldx<P>(hcol(q, j) + v);
-        if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
-        if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
+        if (!ident_only) {
+          rb = g.row_ptr[v];
+          re = g.row_ptr[v + 1];
+          if (l + 1 <= kLvxLevels) o_hi = g.lvx[size_t(l) * size_t(g.n) + v];
+          if (l >= 1 && l <= kLvxLevels) o_lo = g.lvx[size_t(l - 1) * size_t(g.n) + v];
+        }
       }
-      // columns claimed since this node was last enqueued were reached at
-      // this level: their hit level is l, written here once
+      // Columns claimed since this node was last enqueued were reached at
+      // this level: their hit level is l, written here once.  The columns it
+      // had been seen with were reached earlier (h < l).  So the split the
+      // expansion needs, h == l versus h < l, comes from the seen byte, and no
+      // hit level is read.
       const uint32_t fresh = has ? (vb & ~seen & full) : 0u;
       if (fresh) {
 #pragma unroll
-        for (int j = 0; j < nt; ++j) {
-          if (!((fresh >> j) & 1u)) continue;
-          hcol(q, j)[v] = uint8_t(l);
-          hv[j] = l;
-        }
+        for (int j = 0; j < nt; ++j)
+          if ((fresh >> j) & 1u) hcol(q, j)[v] = uint8_t(l);
         s.vseen[v] = uint8_t(vb);
       }
       if (has && !((cfw >> (v & 31u)) & 1u)) {
-        uint32_t mx = 0;
-#pragma unroll
-        for (int j = 0; j < nt; ++j) {
-          if (!((vb >> j) & 1u)) continue;
-          const uint32_t h = hv[j];
-          mx = h > mx ? h : mx;
-          if (h == l) eq |= uint8_t(1u << j);
-          else if (h < l) lt |= uint8_t(1u << j);
-        }
+        eq = uint8_t(fresh);
+        lt = uint8_t(vb & seen & full);
         if ((vb & full) == full && (run == 0 || nt >= 2)) {
           s.stopl[v] = uint8_t(l);
           stop_now = true;
           if (run == 0) {
+            // a node is identified at the level its last column arrives
+            // (it is in the frontier of that level), so S^c = max_j h = l
+            // (Theorem 3)
             is_cg = true;
-            cg_key = (mx << kNodeBits) | uint32_t(g.ext_of[v]);   // ranked by (S^c, caller id)
-            if (mx != l) atomicOr(&c->err, kErrInternal);
+            cg_key = (l << kNodeBits) | uint32_t(g.ext_of[v]);   // ranked by (S^c, caller id)
+            if (!fresh) atomicOr(&c->err, kErrInternal);
           }
         } else {
           expand = !ident_only;
@@ -558,7 +547,7 @@ __device__ __forceinline__ void enqueue_columns(const DevKG& g, const DevSlot& s
   }
 }
 
-__global__ void __launch_bounds__(kEnqThreads, 5)      // at most 51 registers: 5 blocks per SM
+__global__ void __launch_bounds__(kEnqThreads, 6)      // at most 40 registers: 6 blocks per SM
 k_enqueue(DevKG g, DevSlot s, int run) {
   Ctl* c = s.ctl;
   const bool done = c->done != 0;
