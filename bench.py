@@ -57,7 +57,7 @@ FALLBACK_HBM = 6400.0
 # expansion source is unchanged.
 NCU_TRAFFIC = {
     # 8 queries of the large workload, one B300, every k_expand launch (80)
-    "large": {"sha1": "6ea25d34b7a6", "queries": 8, "launches": 80, "dram_bytes": 24113970944},
+    "large": {"sha1": "6ea25d34b7a6", "queries": 8, "launches": 80, "dram_bytes": 24113390080},
 }
 
 
@@ -323,12 +323,13 @@ def level_bytes(r, n):
     return exp, enq
 
 
-def expand_roofline(kg, qs, stats, workload="medium"):
+def expand_roofline(kg, qs, stats, workload="large"):
     """Profiling pass (kernels launched directly, CUDA events around each
     launch): device time per kernel class, and per Glevel the algorithmic
     bytes of the expansion and the enqueue against the measured HBM peak -
-    over all launches, and over the dense levels alone.  The stored ncu DRAM
-    traffic applies to the medium workload's 64 queries only."""
+    over all launches, and over the dense levels alone.  The ncu DRAM bytes
+    stored in NCU_TRAFFIC (per workload, for the expansion source they were
+    captured with) are set beside the same launches' algorithmic bytes."""
     kg.set_profiling(True)
     kg.profile(reset=True)
     kg.profile_levels(reset=True)
@@ -724,7 +725,7 @@ def main():
     return run(args)
 
 
-def profile_only(nq: int, workload: str = "medium") -> int:
+def profile_only(nq: int, workload: str = "large") -> int:
     import torch
     import paper_2001_06770_b300 as rpq
     import rpqgen
