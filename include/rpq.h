@@ -147,7 +147,7 @@ typedef struct {
 typedef struct {
     int64_t e_act_central;  /* (column, edge) activations, central run */
     int64_t e_act_marginal; /* same, marginal run */
-    int64_t hits_central;   /* first hits (h writes), central run */
+    int64_t hits_central;   /* first hits ((node, column) pairs reached, seeds excluded), central run */
     int64_t hits_marginal;
     int32_t levels_central; /* last identified Glevel of each run (-1: not run) */
     int32_t levels_marginal;

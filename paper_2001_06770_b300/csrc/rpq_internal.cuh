@@ -9,9 +9,13 @@
 //
 // Per-search state (one "slot"; several slots run concurrently):
 //   H        uint8[8][hp]  Node-Keyword Matrix (Section 4.2.1), column-major
-//                          hit levels, valid only where the visited bit is set
+//                          hit levels; a column's level is written by the
+//                          enqueue that first sees its visited bit (the
+//                          node's seen byte records which), and is read only
+//                          after that, so H is never cleared
 //   vis      uint8[n]      visited bits, bit j = column j reached (read as
-//                          bytes, updated with 32-bit atomicOr)
+//                          bytes, set with 32-bit atomicOr / red.or)
+//   vseen    uint8[n]      the visited bits the enqueue has written H for
 //   F[2]     uint32[n/32]  Frontier Flag Array, double buffered by level
 //   cf       uint32[n/32]  Joining Flag Array (node stopped expanding)
 //   stopl    uint8[n]      level at which the cf bit was set

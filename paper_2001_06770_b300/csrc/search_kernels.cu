@@ -564,12 +564,14 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 // receiving side: node v is first hit in column j at l+1 exactly when some
 // neighbour u expands to it at level l, i.e. u was reached with
 // max(h_uj, a_uv) = l and u had not stopped by then (Algorithm 1,
-// Definition 8; the levels are symmetric).  One warp per (V_C node, column)
-// scans v's entries with a <= l and stops at the first such u; the scan
-// writes nothing.  The last block to finish applies the hits (h = l+1,
-// visited bit, F_{l+1}, the frontier queue of l+1 when it is in use: the
-// same writes the expansion would make) and runs the identification of
-// level l+1 on V_C alone.  When that shows the run stops at l+1 (every
+// Definition 8; the levels are symmetric; u's levels of the columns reached
+// by level l were written by the enqueues up to this level's).  One warp per
+// (V_C node, column) scans v's entries with a <= l and stops at the first
+// such u; the scan writes nothing.  The last block to finish applies the
+// hits (visited bit, F_{l+1} and the frontier queue of l+1 when it is in
+// use, as a claim of the expansion would; and h = l+1, which the next
+// enqueue writes again) and runs the identification of level l+1 on V_C
+// alone.  When that shows the run stops at l+1 (every
 // selected CG matched, Theorem 4, or l+1 = L) and some hit was applied (so
 // Q_{l+1} is not empty), nothing else the expansion of level l would compute
 // can reach the results, and k_expand skips it.  Levels with fewer than
