@@ -42,7 +42,7 @@ extern "C" {
 #define RPQ_EINTERNAL (-6)  /* a device-side consistency check failed */
 #define RPQ_ESIZE     (-7)  /* a caller buffer is too small; the call reports the size needed */
 
-/* Documented limits of this build. */
+/* Documented limits of the library. */
 #define RPQ_MAX_NODES    (1 << 26)  /* node ids are packed in 26 bits */
 #define RPQ_MAX_LABELS   8192       /* edge labels must be < n_labels <= this */
 #define RPQ_MAX_LEVEL    63         /* activation levels and max_depth <= 63 */
