@@ -180,6 +180,23 @@ int rpq_search(rpq_kg *kg, const rpq_query *q, rpq_result *out, int32_t *n_out, 
 int rpq_search_batch(rpq_kg *kg, const rpq_query *qs, int32_t nq, rpq_result *out, int32_t *n_out,
                      int32_t *status, rpq_stats *stats);
 
+/* The same contract as rpq_search_batch, with the whole batch in one
+ * persistent kernel launch fed by a device work queue: up to
+ * min(batch_slots, 32) queries are in flight, each offering the chunks of
+ * its current phase (run clear, seeding, each Glevel's enqueue, V_C check
+ * and expansion, top-w selection, each level of the recovery sweep) to the
+ * resident blocks, and a slot whose query ends takes the next query of the
+ * batch on the device, with no host step between queries.  Results and
+ * stats equal those of rpq_search one query at a time, except
+ * stats.kernels = 0 (the batch is a single launch).  The kernel's blocks
+ * never wait for each other inside a phase; a watchdog ends the launch when
+ * no phase finishes for about 1 s (RPQ_BARRIER_LIMIT clock cycles): the
+ * queries not finished by then get RPQ_ETIMEOUT in status and the call
+ * returns RPQ_ETIMEOUT (results of finished queries are kept).  Synchronous;
+ * host buffers; temporary device memory of about 3 KB per query. */
+int rpq_search_batch_persistent(rpq_kg *kg, const rpq_query *qs, int32_t nq, rpq_result *out, int32_t *n_out,
+                                int32_t *status, rpq_stats *stats);
+
 /* ---------------------------------------------------------------- tracing */
 /* Debug trace of one query, for comparison with a reference implementation.
  * Every pointer may be NULL; sizes are in elements.

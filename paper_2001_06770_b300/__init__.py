@@ -28,6 +28,7 @@ RPQ_OK, RPQ_EINVAL, RPQ_ENOMEM, RPQ_ETIMEOUT, RPQ_ECUDA, RPQ_ELIMIT, RPQ_EINTERN
 MAX_KEYWORDS, MAX_K, MAX_LEVEL, MAX_LABELS = 8, 64, 63, 8192
 INF = 255
 SYMBOLS = ["rpq_load_kg", "rpq_free_kg", "rpq_kg_export", "rpq_kg_info", "rpq_search", "rpq_search_batch",
+           "rpq_search_batch_persistent",
            "rpq_trace", "rpq_search_subgraphs", "rpq_search_device", "rpq_sync_device", "rpq_slot_stream", "rpq_set_profiling",
            "rpq_profile_read", "rpq_profile_levels", "rpq_topk_keys_noalloc", "rpq_server_create", "rpq_server_create_sized", "rpq_server_info", "rpq_server_pages",
            "rpq_server_submit", "rpq_server_poll", "rpq_server_replay", "rpq_server_destroy",
@@ -143,6 +144,7 @@ def lib():
         L.rpq_kg_info.argtypes = [P, P, P, P]
         L.rpq_search.argtypes = [P, ctypes.POINTER(Query), P, P, P]
         L.rpq_search_batch.argtypes = [P, P, i32, P, P, P, P]
+        L.rpq_search_batch_persistent.argtypes = [P, P, i32, P, P, P, P]
         L.rpq_trace.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(TraceBuf)]
         L.rpq_search_subgraphs.argtypes = [P, ctypes.POINTER(Query), P, P, P, ctypes.POINTER(Subgraphs)]
         L.rpq_search_device.argtypes = [P, P, i32, i32, i32, i32, f64, P, P]
@@ -276,9 +278,12 @@ class KG:
         _check(lib().rpq_search(self._h, ctypes.byref(q), _ptr(out), ctypes.byref(n_out), ctypes.byref(st)))
         return out[:n_out.value].copy(), st.as_dict()
 
-    def search_batch(self, queries):
+    def search_batch(self, queries, persistent=False):
         """queries: iterable of objects with central, marginal, k, max_depth
-        (and optionally gamma).  Returns a list of (results, stats, status)."""
+        (and optionally gamma).  Returns a list of (results, stats, status).
+        persistent: the whole batch in one persistent kernel launch fed by a
+        device work queue (rpq_search_batch_persistent) instead of concurrent
+        per-query graphs on the batch slots."""
         queries = list(queries)
         keep = []
         arr = (Query * max(len(queries), 1))()
@@ -290,8 +295,9 @@ class KG:
         n_out = np.zeros(max(len(queries), 1), np.int32)
         status = np.zeros(max(len(queries), 1), np.int32)
         st = (Stats * max(len(queries), 1))()
-        _check(lib().rpq_search_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(queries), _ptr(out),
-                                      _ptr(n_out), _ptr(status), ctypes.cast(st, ctypes.c_void_p)))
+        fn = lib().rpq_search_batch_persistent if persistent else lib().rpq_search_batch
+        _check(fn(self._h, ctypes.cast(arr, ctypes.c_void_p), len(queries), _ptr(out),
+                  _ptr(n_out), _ptr(status), ctypes.cast(st, ctypes.c_void_p)))
         return [(out[base[i]:base[i] + n_out[i]].copy(), st[i].as_dict(), int(status[i])) for i in range(len(queries))]
 
     def trace(self, central, marginal, k, max_depth, gamma=0.5, frontier_cap=None, w=0, product=False):

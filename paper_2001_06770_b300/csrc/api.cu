@@ -652,6 +652,107 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
   return RPQ_OK;
 }
 
+int rpq_search_batch_persistent(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* out, int32_t* n_out,
+                                int32_t* status, rpq_stats* stats) {
+  if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
+  if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
+  std::vector<int64_t> base(size_t(nq) + 1, 0);
+  for (int32_t i = 0; i < nq; ++i) base[size_t(i) + 1] = base[size_t(i)] + std::max(qs[i].k, 0);
+  std::vector<QueryDev> recs;
+  std::vector<int32_t> idx;                   // batch record -> caller's query
+  for (int32_t i = 0; i < nq; ++i) {
+    QueryDev qv;
+    bool empty = false;
+    n_out[i] = 0;
+    status[i] = check_query(kg, &qs[i], &qv, &empty);
+    if (status[i] != RPQ_OK) continue;
+    if (empty) { empty_result(&n_out[i], stats ? &stats[i] : nullptr); continue; }
+    recs.push_back(qv);
+    idx.push_back(i);
+  }
+  const int nv = int(recs.size());
+  if (nv == 0) return RPQ_OK;
+  int nslots = std::max(1, std::min({slot_count(kg), nv, kBatchMaxSlots}));
+  std::vector<Slot*> slots(size_t(nslots), nullptr);
+  for (int i = 0; i < nslots; ++i) {          // the slots of rpq_search_batch (slot 0 serves single searches)
+    const int rc = get_slot(kg, size_t(i) + 1, &slots[size_t(i)]);
+    if (rc == RPQ_ENOMEM && i > 0) { nslots = i; slots.resize(size_t(i)); break; }
+    if (rc != RPQ_OK) return rc;
+  }
+  std::vector<DevSlot> ds(static_cast<size_t>(nslots));
+  for (int i = 0; i < nslots; ++i) {
+    ds[size_t(i)] = slots[size_t(i)]->d;
+    ds[size_t(i)].lrec = nullptr;               // no per-level records in a persistent batch
+    ds[size_t(i)].qlog = nullptr;
+  }
+  QueryDev* d_q = nullptr;
+  uint8_t* d_out = nullptr;
+  void* d_state = nullptr;
+  auto release = [&]() { cudaFree(d_q); cudaFree(d_out); cudaFree(d_state); };
+  int rc = alloc_device((void**)&d_q, sizeof(QueryDev) * size_t(nv), nullptr);
+  if (rc == RPQ_OK) rc = alloc_device((void**)&d_out, kBatchRecBytes * size_t(nv), nullptr);
+  if (rc == RPQ_OK) rc = alloc_device((void**)&d_state, batch_state_bytes(nslots), nullptr);
+  if (rc != RPQ_OK) { release(); return rc; }
+  cudaStream_t st = slots[0]->st;
+  std::vector<uint8_t> h_out(kBatchRecBytes * size_t(nv));
+  BatchCtl bc{};
+  if (cudaMemcpyAsync(d_q, recs.data(), sizeof(QueryDev) * size_t(nv), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(d_out, 0, kBatchRecBytes * size_t(nv), st) != cudaSuccess) {
+    release();
+    set_error(RPQ_ECUDA, "batch upload failed");
+    return RPQ_ECUDA;
+  }
+  rc = launch_batch(kg->dev, ds.data(), nslots, d_q, nv, d_out, d_state, barrier_limit(), st);
+  if (rc != RPQ_OK) {
+    release();
+    set_error(RPQ_ECUDA, "batch launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return RPQ_ECUDA;
+  }
+  const cudaError_t ce = cudaStreamSynchronize(st);
+  if (ce == cudaSuccess &&
+      (cudaMemcpy(h_out.data(), d_out, h_out.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+       cudaMemcpy(&bc, static_cast<char*>(d_state) + sizeof(BatchSlotState) * size_t(nslots), sizeof(bc),
+                  cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    release();
+    set_error(RPQ_ECUDA, "batch download failed");
+    return RPQ_ECUDA;
+  }
+  release();
+  if (ce != cudaSuccess) { set_error(RPQ_ECUDA, "persistent batch: %s", cudaGetErrorString(ce)); return RPQ_ECUDA; }
+  if (bc.err) {
+    // the watchdog ended the kernel: queries in flight left recovery state
+    // behind, which must be zero when a query starts
+    for (Slot* s : slots) {
+      cudaMemset(s->d.rcnt, 0, sizeof(uint32_t) * kRecStride * kMaxCols);
+      cudaMemset(s->d.vmask, 0, sizeof(unsigned long long) * s->d.cap);
+      cudaMemset(s->d.rmask, 0, sizeof(unsigned long long) * s->d.cap * kMaxCols);
+    }
+  }
+  for (int r = 0; r < nv; ++r) {
+    const int32_t i = idx[size_t(r)];
+    const uint8_t* rec = h_out.data() + kBatchRecBytes * size_t(r);
+    uint32_t flag = 0;
+    memcpy(&flag, rec, sizeof(flag));
+    if (flag != 1u) {                           // not finished when the watchdog ended the kernel
+      status[i] = RPQ_ETIMEOUT;
+      set_error(RPQ_ETIMEOUT, "persistent batch: no phase finished within the watchdog limit");
+      continue;
+    }
+    Ctl c;
+    memcpy(&c, rec + kBatchRecHead, sizeof(Ctl));
+    status[i] = dev_err_to_status(c.err);
+    if (status[i] != RPQ_OK) continue;
+    const int32_t nr = int32_t(std::min<uint32_t>(c.n_res, uint32_t(qs[i].k)));
+    if (nr) memcpy(out + base[size_t(i)], rec + kBatchRecHead + kCtlBytes, sizeof(rpq_result) * size_t(nr));
+    n_out[i] = nr;
+    if (stats) {
+      fill_stats(c, &stats[i]);
+      stats[i].kernels = 0;                     // the whole batch is one launch
+    }
+  }
+  return bc.err ? RPQ_ETIMEOUT : RPQ_OK;
+}
+
 int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, rpq_stats* stats, rpq_trace_buf* tr) {
   if (!kg || !out || !n_out || !tr) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   QueryDev qv;

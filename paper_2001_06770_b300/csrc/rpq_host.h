@@ -152,4 +152,12 @@ void launch_results(const DevSlot& s, cudaStream_t st, Prof* prof);
 int kernels_fixed_per_query(int n_m);
 int launch_central_part(const DevKG& g, const DevSlot& s, int L, cudaStream_t st, Prof* prof);
 int launch_marginal_part(const DevKG& g, const DevSlot& s, int n_m, int L, cudaStream_t st, Prof* prof);
+// The multi-query persistent kernel: n_queries query records (keyword ids
+// and parameters) run on n_slots slots (own columns), one record of
+// kBatchRecBytes per query at d_out; d_state holds batch_state_bytes(n_slots)
+// bytes (cleared here).  limit: watchdog, clock cycles without a finished
+// phase.  Asynchronous on st.
+size_t batch_state_bytes(int n_slots);
+int launch_batch(const DevKG& g, const DevSlot* slots, int n_slots, const QueryDev* d_queries, int n_queries,
+                 void* d_out, void* d_state, long long limit, cudaStream_t st);
 }  // namespace rpq

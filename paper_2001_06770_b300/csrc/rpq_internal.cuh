@@ -210,19 +210,43 @@ struct DevSlot {
   int32_t* n_res;
 };
 
+// Multi-query persistent kernel: the work-queue state of one slot (device
+// memory, zeroed before the launch).  A phase of a slot's query is split
+// into chunks; a block takes chunk next of the current phase with one
+// atomic add on word, and the block that finishes its last chunk moves the
+// slot to its next phase.
+constexpr int kBatchMaxSlots = 32;
+struct BatchSlotState {
+  unsigned long long word;   // (chunks of the current phase << 32) | next chunk to hand out
+  uint32_t done;             // chunks of the current phase finished
+  uint32_t phase;            // current phase (search_kernels.cu)
+  uint32_t run;              // its run (0 central, 1 marginal)
+  uint32_t level;            // recovery level of a recovery sweep phase
+  int32_t query;             // batch index of the slot's query, -1 when the slot is idle
+  uint32_t pad[25];          // one 128-byte line per slot: polls and claims of one slot do not
+                             // contend with another's
+};
+static_assert(sizeof(BatchSlotState) == 128, "one line per slot");
+struct BatchCtl {
+  uint32_t next_query;         // batch index of the next query to start
+  uint32_t finished;           // queries whose record is written
+  uint32_t err;                // kErrTimeout: no phase finished within the watchdog limit
+  uint32_t pad;
+  unsigned long long progress; // phases finished so far (watchdog)
+};
+// Record of one query of a persistent batch: a flag word (1 once the record
+// is complete) padded to 16 bytes, the control block and the results.
+constexpr size_t kBatchRecHead = 16;
+constexpr size_t kBatchRecBytes = kBatchRecHead + kCtlBytes + 24 * kMaxK;   // 24 = sizeof(rpq_result)
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
-// Column pointers of the current query.  They do not change while the
-// query's kernels run, so they are read through the read-only path.
-__device__ __forceinline__ uint8_t* hcol(const QueryDev& q, int j) {
-  return reinterpret_cast<uint8_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.hc[j])));
-}
-__device__ __forceinline__ unsigned long long* rmcol(const QueryDev& q, int j) {
-  return reinterpret_cast<unsigned long long*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.rm[j])));
-}
-__device__ __forceinline__ uint32_t* rlcol(const QueryDev& q, int j) {
-  return reinterpret_cast<uint32_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q.rl[j])));
-}
+// Column pointers of the current query.  Plain loads, not the read-only
+// path: the multi-query persistent kernel rewrites a slot's query record
+// while it runs.
+__device__ __forceinline__ uint8_t* hcol(const QueryDev& q, int j) { return q.hc[j]; }
+__device__ __forceinline__ unsigned long long* rmcol(const QueryDev& q, int j) { return q.rm[j]; }
+__device__ __forceinline__ uint32_t* rlcol(const QueryDev& q, int j) { return q.rl[j]; }
 
 __device__ __forceinline__ uint8_t vis_byte(const uint32_t* vis, uint32_t v) {
   return reinterpret_cast<const uint8_t*>(vis)[v];

@@ -41,6 +41,7 @@
 // instead of as scattered bytes by every claim.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -89,6 +90,14 @@ __device__ __forceinline__ T ldx(const T* ptr) {
 __device__ __forceinline__ void vis_or(uint32_t* vis, uint32_t v, uint32_t bits) {
   atomicOr(vis + (v >> 2), bits << ((v & 3u) * 8u));
 }
+
+// The block's share of a phase's work: block b of n.  A launched kernel is
+// its own phase (blockIdx.x of gridDim.x); in the multi-query persistent
+// kernel a block runs chunk b of the n chunks of one query's phase.
+struct Part {
+  uint32_t b, n;
+};
+__device__ __forceinline__ Part launch_part() { return Part{blockIdx.x, gridDim.x}; }
 
 // ------------------------------------------------------------ query set-up
 __global__ void k_set_query(DevSlot s, QueryDev qv, const int32_t* d_kw) {
@@ -168,7 +177,7 @@ __device__ __forceinline__ void queue_push(const DevSlot& s, Ctl* c, int p, bool
 __device__ void write_results(const DevSlot& s);
 
 // Initialisation (Section 4.2.1): keyword nodes get h = 0 and become frontiers.
-__global__ void k_seed(DevKG g, DevSlot s, int run) {
+__device__ __forceinline__ void seed_body(const DevKG& g, const DevSlot& s, int run, Part pt) {
   Ctl* c = s.ctl;
   if (c->done) return;
   const QueryDev& q = *s.q;
@@ -180,18 +189,18 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
     const int32_t kw = q.kw[kb + j];
     if (kw < 0 || kw >= g.n_kw) {
       beg[j] = len[j] = 0;
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrKeyword);
+      if (pt.b == 0 && threadIdx.x == 0) atomicOr(&c->err, kErrKeyword);
       continue;
     }
     beg[j] = g.kw_ptr[kw];
     len[j] = g.kw_ptr[kw + 1] - beg[j];
     total += len[j];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->seeded[run] = total;   // (node, column) pairs with h = 0
+  if (pt.b == 0 && threadIdx.x == 0) c->seeded[run] = total;   // (node, column) pairs with h = 0
   uint32_t* F0 = s.F[0];
-  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t stride = pt.n * blockDim.x;
   const uint32_t end = (total + 31u) & ~31u;            // whole warps for the queue push
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < end; i += stride) {
+  for (uint32_t i = pt.b * blockDim.x + threadIdx.x; i < end; i += stride) {
     bool fresh = false;
     uint32_t v = 0;
     if (i < total) {
@@ -212,6 +221,8 @@ __global__ void k_seed(DevKG g, DevSlot s, int run) {
     queue_push(s, c, 0, true, fresh, v);
   }
 }
+
+__global__ void k_seed(DevKG g, DevSlot s, int run) { seed_body(g, s, run, launch_part()); }
 
 // ------------------------------------------------------------- RPG scores
 // S^r of Eq. 6, or the multiplicative combination S^c * S^m.  Explicit
@@ -268,14 +279,20 @@ __device__ bool theorem4_stop(const Ctl* c, const uint8_t* matched, const uint8_
 // expansion that start inside it.
 // NT is the run's number of keyword columns (1..kMaxCols), a compile-time
 // constant so that the per-node column loops hold exactly the run's columns.
+// Whether the enqueue of the level of parity p reads the frontier queue
+// (else the bit map): the queue was filled, did not overflow and is short.
+template <bool P>
+__device__ __forceinline__ bool enqueue_sparse(const DevSlot& s, const Ctl* c, int p) {
+  return ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && ldx<P>(&c->fq_n[p]) <= s.fq_limit;
+}
+
 template <bool P, int NT>
-__device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l) {
+__device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l, Part pt) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   constexpr int nt = NT;
   const uint32_t full = (1u << nt) - 1u;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  constexpr uint32_t nwarp = kEnqThreads / 32;
   const int p = int(l & 1u);
   uint32_t* Fc = s.F[p];
   uint32_t* Fn = s.F[p ^ 1];
@@ -283,7 +300,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_acc[kMaxK];
 
-  if (run == 1 && blockIdx.x == gridDim.x - 1u) {
+  if (run == 1 && pt.b == pt.n - 1u) {
     // RPG identification: a selected CG matches when every marginal keyword
     // has reached some node of its V_C; then S^m = max_i min_{v in V_C} h = l.
     // (The last block: on a short level the first blocks hold the frontier.)
@@ -316,14 +333,14 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   // identification that can change the results (the PTC stops and work
   // items of a level that is not expanded are never used): count Q_l only.
   const bool count_only = run == 1 && l > 0 && ldx<P>(&c->skip_lvl) == l;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->cg_next[p ^ 1] = 0;   // counted by k_expand of this level
+  if (pt.b == 0 && threadIdx.x == 0) c->cg_next[p ^ 1] = 0;   // counted by k_expand of this level
   const uint32_t fq_n = ldx<P>(&c->fq_n[p]);
-  const bool sparse = ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && fq_n <= s.fq_limit;
+  const bool sparse = enqueue_sparse<P>(s, c, p);
   // The next level's queue is kept only while this level is sparse (a dense
   // level is usually followed by a dense one, and its appends would all
   // contend on one counter).  Every block computes the same `sparse` from
   // values no kernel changes during this level; k_expand reads fq_use.
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (pt.b == 0 && threadIdx.x == 0) {
     c->fq_use[p ^ 1] = sparse ? 1u : 0u;
     if (s.lrec && sparse) s.lrec[run * kLogLevels + l].flags |= kLvlQueue;
   }
@@ -334,7 +351,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   const uint32_t kTile = sparse ? uint32_t(kEnqThreads) : uint32_t(kEnqThreads * kEnqRounds);
   uint32_t qcount = 0;
   uint64_t eact = 0;                                   // E_act of this level (Algorithm 1's activations)
-  for (uint32_t tile = blockIdx.x * kTile; tile < nsrc; tile += gridDim.x * kTile) {
+  for (uint32_t tile = pt.b * kTile; tile < nsrc; tile += pt.n * kTile) {
     uint32_t it_seg[kEnqRounds], it_len[kEnqRounds], it_msk[kEnqRounds];
     // Candidate node of each round.  Queue mode: entry tile + threadIdx, one
     // round.  Bit-map mode: the warp owns words w0 .. w0 + kEnqRounds - 1 of
@@ -533,29 +550,34 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
 
 // The enqueue of the run's column count (the same in every thread).
 template <bool P>
-__device__ __forceinline__ void enqueue_columns(const DevKG& g, const DevSlot& s, int run, uint32_t l) {
+__device__ __forceinline__ void enqueue_columns(const DevKG& g, const DevSlot& s, int run, uint32_t l, Part pt) {
   const QueryDev& q = *s.q;
   switch (run == 0 ? q.n_c : q.n_m) {
-    case 1: enqueue_level<P, 1>(g, s, run, l); break;
-    case 2: enqueue_level<P, 2>(g, s, run, l); break;
-    case 3: enqueue_level<P, 3>(g, s, run, l); break;
-    case 4: enqueue_level<P, 4>(g, s, run, l); break;
-    case 5: enqueue_level<P, 5>(g, s, run, l); break;
-    case 6: enqueue_level<P, 6>(g, s, run, l); break;
-    case 7: enqueue_level<P, 7>(g, s, run, l); break;
-    default: enqueue_level<P, kMaxCols>(g, s, run, l); break;
+    case 1: enqueue_level<P, 1>(g, s, run, l, pt); break;
+    case 2: enqueue_level<P, 2>(g, s, run, l, pt); break;
+    case 3: enqueue_level<P, 3>(g, s, run, l, pt); break;
+    case 4: enqueue_level<P, 4>(g, s, run, l, pt); break;
+    case 5: enqueue_level<P, 5>(g, s, run, l, pt); break;
+    case 6: enqueue_level<P, 6>(g, s, run, l, pt); break;
+    case 7: enqueue_level<P, 7>(g, s, run, l, pt); break;
+    default: enqueue_level<P, kMaxCols>(g, s, run, l, pt); break;
   }
+}
+
+template <bool P>
+__device__ __forceinline__ void enqueue_body(const DevKG& g, const DevSlot& s, int run, Part pt) {
+  Ctl* c = s.ctl;
+  const bool done = ldx<P>(&c->done) != 0;
+  if (pt.b == 0 && threadIdx.x == 0) c->exp_skip = done ? 1u : 0u;   // read by this level's k_expand
+  if (done) return;
+  const uint32_t l = ldx<P>(&c->lvl_enq);
+  if (pt.b == 0 && threadIdx.x == 0) c->lvl_exp = l;
+  enqueue_columns<P>(g, s, run, l, pt);
 }
 
 __global__ void __launch_bounds__(kEnqThreads, 6)      // at most 40 registers: 6 blocks per SM
 k_enqueue(DevKG g, DevSlot s, int run) {
-  Ctl* c = s.ctl;
-  const bool done = c->done != 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->exp_skip = done ? 1u : 0u;   // read by this level's k_expand
-  if (done) return;
-  const uint32_t l = c->lvl_enq;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->lvl_exp = l;
-  enqueue_columns<false>(g, s, run, l);
+  enqueue_body<false>(g, s, run, launch_part());
 }
 
 // ------------------------------------------- level: V_C check (marginal run)
@@ -579,23 +601,37 @@ k_enqueue(DevKG g, DevSlot s, int run) {
 // kTgtMaxTasks (node, column) pairs (keywords on hundreds of thousands of
 // nodes: the single block applying the hits would dominate), are left alone.
 // Off in trace mode, where every frontier is compared.
-__global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
+// Whether the V_C check runs at the current marginal Glevel: not when the
+// run ends at this level anyway (the stop test of the expansion), nor when
+// the level is too small for a skip to pay for the check.
+template <bool P>
+__device__ __forceinline__ bool target_runs(const DevSlot& s) {
+  const Ctl* c = s.ctl;
+  if (ldx<P>(&c->done) || !s.target) return false;
+  const QueryDev& q = *s.q;
+  const uint32_t l = ldx<P>(&c->lvl_exp);
+  const int p = int(l & 1u);
+  const int nm = q.n_m;
+  if (nm == 0 || ldx<P>(&c->nq[p]) == 0 || ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel) || ldx<P>(&c->rpg_stop) ||
+      l >= uint32_t(q.L))
+    return false;
+  return (ldx<P>(&c->work[p]) & kWorkMask) >= s.tgt_min_work &&
+         min(ldx<P>(&c->nvc), s.cap) * uint32_t(nm) <= kTgtMaxTasks;
+}
+
+__device__ __forceinline__ void target_body(const DevKG& g, const DevSlot& s, Part pt) {
   Ctl* c = s.ctl;
-  if (c->done || !s.target) return;
+  if (!target_runs<false>(s)) return;
   const QueryDev& q = *s.q;
   const uint32_t l = c->lvl_exp;
   const int p = int(l & 1u);
   const uint32_t nsel = c->nsel;
   const int nm = q.n_m;
-  // the run ends at level l anyway (the stop test of k_expand), or the level
-  // is too small for a skip to pay for the check
-  if (nm == 0 || c->nq[p] == 0 || c->n_matched >= nsel || c->rpg_stop || l >= uint32_t(q.L)) return;
-  if ((c->work[p] & kWorkMask) < s.tgt_min_work || min(c->nvc, s.cap) * uint32_t(nm) > kTgtMaxTasks) return;
   const uint32_t nvc = min(c->nvc, s.cap);
   const uint32_t ntask = nvc * uint32_t(nm);
   const uint32_t lane = lane_id();
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t gw = (pt.b * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (pt.n * blockDim.x) >> 5;
   for (uint32_t t = gw; t < ntask; t += nwarps) {
     const uint32_t pr = s.vcl[t / uint32_t(nm)];
     const uint32_t j = t % uint32_t(nm);
@@ -630,7 +666,7 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&c->tgt_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    s_last = atomicAdd(&c->tgt_done, 1u) == pt.n - 1u ? 1u : 0u;
     s_hits = 0;
   }
   __syncthreads();
@@ -679,6 +715,8 @@ __global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) {
   }
 }
 
+__global__ void __launch_bounds__(kTgtThreads) k_target(DevKG g, DevSlot s) { target_body(g, s, launch_part()); }
+
 // ----------------------------------------------------------- level: expand
 // Termination (every block reaches the same decision from the control block,
 // which k_enqueue finished writing) and expansion (Algorithm 1) of the work
@@ -708,39 +746,59 @@ __device__ __forceinline__ void load_window(const Item* items, const uint16_t* i
 // hold, less the seeds (h = 0).  Every block of the stopping launch takes a
 // share of the visited words; the expansions themselves count no hits.
 template <bool P>
-__device__ void count_hits(const DevKG& g, const DevSlot& s, int run, uint64_t* s_warp) {
+__device__ void count_hits(const DevKG& g, const DevSlot& s, int run, uint64_t* s_warp, Part pt) {
   Ctl* c = s.ctl;
   const int nt = run == 0 ? s.q->n_c : s.q->n_m;
   const uint32_t colmask = ((1u << nt) - 1u) * 0x01010101u;      // the run's columns in each byte
   const uint32_t nwords = (uint32_t(g.n) + 3u) >> 2;
   uint64_t cnt = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x)
+  for (uint32_t i = pt.b * blockDim.x + threadIdx.x; i < nwords; i += pt.n * blockDim.x)
     cnt += __popc(ldx<P>(s.vis + i) & colmask);
   const uint64_t tot = block_sum(cnt, s_warp);
   if (threadIdx.x == 0) {
     unsigned long long add = tot;
-    if (blockIdx.x == 0) add -= ldx<P>(&c->seeded[run]);        // modulo 2^64: the sum comes out right
+    if (pt.b == 0) add -= ldx<P>(&c->seeded[run]);        // modulo 2^64: the sum comes out right
     if (add) atomicAdd(&c->hits[run], add);
   }
+}
+
+// Termination decision of Glevel l, the same in every block (from the
+// control block, which the enqueue and the V_C check finished writing): the
+// run stops (empty frontier, enough CGs or every selected CG matched or
+// Theorem 4, or l = L), or the V_C check showed that the V_C nodes alone
+// decide the outcome at level l+1 (skip), else the level's work is expanded.
+struct LevelPlan {
+  bool stop, skip;
+  uint32_t nq, n_items, n_work;
+};
+template <bool P>
+__device__ __forceinline__ LevelPlan level_plan(const DevSlot& s, int run, uint32_t l) {
+  const Ctl* c = s.ctl;
+  const QueryDev& q = *s.q;
+  const int p = int(l & 1u);
+  LevelPlan r;
+  const unsigned long long wk = ldx<P>(&c->work[p]);
+  r.n_items = uint32_t(wk >> kWorkBits);
+  r.n_work = uint32_t(wk & kWorkMask);
+  r.nq = ldx<P>(&c->nq[p]);
+  const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.w))
+                             : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel) || ldx<P>(&c->rpg_stop));
+  r.stop = (r.nq == 0) || term || (l >= uint32_t(q.L));
+  r.skip = !r.stop && ldx<P>(&c->skip_lvl) == l + 1;
+  return r;
 }
 
 // Returns true when the run stops at level l (no expansion then).
 template <bool P>
 __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, int run, uint32_t l,
-                                             cudaGraphConditionalHandle loop, int in_graph) {
+                                             cudaGraphConditionalHandle loop, int in_graph, Part pt) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   const int p = int(l & 1u);
-  const unsigned long long wk = ldx<P>(&c->work[p]);
-  const uint32_t n_items = uint32_t(wk >> kWorkBits);
-  const uint32_t n_work = uint32_t(wk & kWorkMask);
-  const uint32_t nq = ldx<P>(&c->nq[p]);
-  const bool term = run == 0 ? (ldx<P>(&c->ncg) >= uint32_t(q.w))
-                             : (ldx<P>(&c->n_matched) >= ldx<P>(&c->nsel) || ldx<P>(&c->rpg_stop));
-  const bool stop = (nq == 0) || term || (l >= uint32_t(q.L));
-  // k_target found that the V_C nodes alone decide the outcome at level l+1
-  const bool skip = !stop && ldx<P>(&c->skip_lvl) == l + 1;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  const LevelPlan plan = level_plan<P>(s, run, l);
+  const uint32_t n_items = plan.n_items, n_work = plan.n_work, nq = plan.nq;
+  const bool stop = plan.stop, skip = plan.skip;
+  if (pt.b == 0 && threadIdx.x == 0) {
     c->level = l;
     c->frontier += nq;
     const unsigned long long ea = ldx<P>(&c->eact_lvl[p]);   // enqueued activations of this level
@@ -777,8 +835,8 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
     }
   }
   __shared__ uint64_t s_warp[33];
-  if (stop) count_hits<P>(g, s, run, s_warp);
-  if (stop && run == 1 && blockIdx.x == 0) write_results(s);   // the marginal run ends here
+  if (stop) count_hits<P>(g, s, run, s_warp, pt);
+  if (stop && run == 1 && pt.b == 0) write_results(s);   // the marginal run ends here
   if (stop || skip || n_work == 0) return stop;
 
   uint32_t* Fn = s.F[p ^ 1];
@@ -787,10 +845,10 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   // its appends would contend on one counter.
   const uint32_t fq_use_next = ldx<P>(&c->fq_use[p ^ 1]);
   const bool use_next = fq_use_next != 0 && uint64_t(n_work) <= uint64_t(s.fq_next_mult) * s.fq_limit;
-  if (fq_use_next && !use_next && blockIdx.x == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
+  if (fq_use_next && !use_next && pt.b == 0 && threadIdx.x == 0) c->fq_over[p ^ 1] = 1;
   const uint32_t lane = lane_id();
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t gw = (pt.b * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (pt.n * blockDim.x) >> 5;
   const uint32_t ntiles = (n_work + kWarpTile - 1) / kWarpTile;
   uint64_t claims = 0, completed = 0;                // completed: nodes that now hold every central column
   const uint32_t fullc = run == 0 ? (1u << q.n_c) - 1u : 0x100u;
@@ -881,18 +939,24 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   return false;
 }
 
-__global__ void __launch_bounds__(kExpThreads)
-k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
+template <bool P>
+__device__ __forceinline__ void expand_body(const DevKG& g, const DevSlot& s, int run, cudaGraphConditionalHandle loop,
+                                            int in_graph, Part pt) {
   Ctl* c = s.ctl;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->iters[run] += 1;
+  if (pt.b == 0 && threadIdx.x == 0) c->iters[run] += 1;
   // exp_skip, not done: block 0 of the launch that stops the run sets done
   // while other blocks of that launch may still be starting, and they too
   // must take the stop path (their share of the hit count)
-  if (c->exp_skip) {
-    if (in_graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
+  if (ldx<P>(&c->exp_skip)) {
+    if (in_graph && pt.b == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
     return;
   }
-  expand_level<false>(g, s, run, c->lvl_exp, loop, in_graph);
+  expand_level<P>(g, s, run, ldx<P>(&c->lvl_exp), loop, in_graph, pt);
+}
+
+__global__ void __launch_bounds__(kExpThreads)
+k_expand(DevKG g, DevSlot s, int run, cudaGraphConditionalHandle loop, int in_graph) {
+  expand_body<false>(g, s, run, loop, in_graph, launch_part());
 }
 
 // ------------------------------------------------------ persistent run kernel
@@ -934,9 +998,9 @@ k_run(DevKG g, DevSlot s, int run) {
   for (;;) {
     const uint32_t l = *(volatile uint32_t*)&c->lvl_enq;
     if (blockIdx.x == 0 && threadIdx.x == 0) { c->lvl_exp = l; c->iters[run] += 1; }
-    enqueue_columns<true>(g, s, run, l);
+    enqueue_columns<true>(g, s, run, l, launch_part());
     if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
-    if (expand_level<true>(g, s, run, l, 0, 0)) return;
+    if (expand_level<true>(g, s, run, l, 0, 0, launch_part())) return;
     if (!grid_barrier(s.bar, s.bar + 1, gridDim.x, &c->err, s.bar_limit)) break;
   }
   // a barrier ran out: the run ends without results; the error reaches the
@@ -1024,7 +1088,9 @@ __device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K
   return lo + uint32_t(prefix);
 }
 
-// Keep the (at most) K smallest valid keys of keys[0..len) in place; returns their count.
+// Keep the (at most) K smallest valid keys of keys[0..len) in place; returns
+// their count.  len <= PER * blockDim.x.
+template <int PER>
 __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
                                         uint64_t* s_warp, uint32_t* s_bin, uint32_t* s_red) {
   if (threadIdx.x == 0) s_bin[3] = 0;
@@ -1033,7 +1099,7 @@ __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K
   const uint32_t span = kmax > kmin ? 32u - uint32_t(__clz(kmax - kmin)) : 0u;
   const uint32_t t = valid > K ? block_kth_key(keys, len, K, kmin, span, hist, s_warp, s_bin) : 0xfffffffeu;
   // compact keys <= t to the front (order is restored by the final ranking)
-  uint32_t mine[kTopkChunk / kTopkThreads];
+  uint32_t mine[PER];
   uint32_t nm = 0;
   for (uint32_t i = threadIdx.x; i < len; i += blockDim.x)
     if (keys[i] <= t) mine[nm++] = keys[i];
@@ -1043,53 +1109,54 @@ __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K
   return min(valid, K);
 }
 
-__global__ void __launch_bounds__(kTopkThreads) k_topk(DevKG g, DevSlot s) {
+// key holds CHUNK + 2 kMaxK entries and hist 2048; the block has NT threads.
+template <int NT, int CHUNK>
+__device__ void topk_body(const DevKG& g, const DevSlot& s, Part pt, uint32_t* key, uint32_t* hist) {
+  constexpr int PER = CHUNK / NT;
   Ctl* c = s.ctl;
   const uint32_t K = uint32_t(s.q->w);                   // beam width w
   const uint32_t n_in = min(c->ncg, s.cap);
-  const uint32_t nchunks = (n_in + kTopkChunk - 1) / kTopkChunk;
-  __shared__ uint32_t key[kTopkChunk + 2 * kMaxK];
-  __shared__ uint32_t hist[2048];
+  const uint32_t nchunks = (n_in + CHUNK - 1) / CHUNK;
   __shared__ uint64_t s_warp[33];
   __shared__ uint32_t s_bin[4];
   __shared__ uint32_t s_red[100];
   __shared__ uint32_t s_keep, s_last;
-  uint32_t* keep = key + kTopkChunk;                     // survivors of this block (<= 2K while merging)
+  uint32_t* keep = key + CHUNK;                          // survivors of this block (<= 2K while merging)
   if (threadIdx.x == 0) s_keep = 0;
   __syncthreads();
-  for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const uint32_t b = ch * kTopkChunk;
-    const uint32_t len = min(uint32_t(kTopkChunk), n_in - b);
+  for (uint32_t ch = pt.b; ch < nchunks; ch += pt.n) {
+    const uint32_t b = ch * CHUNK;
+    const uint32_t len = min(uint32_t(CHUNK), n_in - b);
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) key[i] = s.cg[b + i];
     __syncthreads();
-    const uint32_t m = block_keep_smallest(key, len, K, hist, s_warp, s_bin, s_red);
+    const uint32_t m = block_keep_smallest<PER>(key, len, K, hist, s_warp, s_bin, s_red);
     // merge with the survivors of earlier chunks
     const uint32_t k0 = s_keep;
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) keep[k0 + i] = key[i];
     __syncthreads();
-    const uint32_t mm = block_keep_smallest(keep, k0 + m, K, hist, s_warp, s_bin, s_red);
+    const uint32_t mm = block_keep_smallest<PER>(keep, k0 + m, K, hist, s_warp, s_bin, s_red);
     if (threadIdx.x == 0) s_keep = mm;
     __syncthreads();
   }
-  uint32_t* out = s.topk + size_t(blockIdx.x) * K;
+  uint32_t* out = s.topk + size_t(pt.b) * K;
   for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) out[i] = i < s_keep ? keep[i] : 0xffffffffu;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&c->topk_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+    s_last = atomicAdd(&c->topk_done, 1u) == pt.n - 1u ? 1u : 0u;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   // the last block: the K smallest of all survivors (blocks that had a chunk)
-  const uint32_t nb = min(nchunks, gridDim.x);
+  const uint32_t nb = min(nchunks, pt.n);
   uint32_t total = 0;
   for (uint32_t blk = 0; blk < nb; ++blk) {            // gather, reducing whenever the buffer fills
     for (uint32_t i = threadIdx.x; i < K; i += blockDim.x) key[total + i] = __ldcg(s.topk + size_t(blk) * K + i);
     total += K;
-    if (total + K > uint32_t(kTopkChunk) || blk + 1 == nb) {
+    if (total + K > uint32_t(CHUNK) || blk + 1 == nb) {
       __syncthreads();
-      total = block_keep_smallest(key, total, K, hist, s_warp, s_bin, s_red);
+      total = block_keep_smallest<PER>(key, total, K, hist, s_warp, s_bin, s_red);
       __syncthreads();
     }
   }
@@ -1118,6 +1185,12 @@ __global__ void __launch_bounds__(kTopkThreads) k_topk(DevKG g, DevSlot s) {
   }
   __syncthreads();
   if (s.q->n_m == 0 || total == 0) write_results(s);   // no marginal run follows
+}
+
+__global__ void __launch_bounds__(kTopkThreads) k_topk(DevKG g, DevSlot s) {
+  __shared__ uint32_t key[kTopkChunk + 2 * kMaxK];
+  __shared__ uint32_t hist[2048];
+  topk_body<kTopkThreads, kTopkChunk>(g, s, launch_part(), key, hist);
 }
 
 // ---------------------------------------------------------------- recovery
@@ -1157,105 +1230,127 @@ __device__ __forceinline__ bool holds_central(const DevSlot& s, const QueryDev& 
   return holds;
 }
 
-__global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads, 1)
-k_recover_cols(DevKG g, DevSlot s) {
-  cg::cluster_group cluster = cg::this_cluster();
+// A node for the overflow part of column list rlist (cap entries).
+__device__ __forceinline__ void rec_overflow(Ctl* c, uint32_t* rlist, uint32_t* ovf, uint32_t cap, uint32_t v) {
+  const uint32_t p = atomicAdd(ovf, 1u);
+  if (p < cap) rlist[cap - 1u - p] = v; else atomicOr(&c->err, kErrOverflow);
+}
+
+// Start of column j's sweep (one CTA): the CG nodes that do not hold keyword
+// j start it with their CG bit; with j = 0 every CG node also enters V^c's
+// union list.
+__device__ void rec_start(const DevSlot& s, int j) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   const uint32_t nsel = c->nsel;
-  const int j = int(blockIdx.x / kRecCluster);
-  const uint32_t rank = cluster.block_rank();
-  if (nsel == 0 || j >= q.n_c) return;                     // the same in every CTA of the cluster
-  const int maxlev = c->levels[0];
+  if (nsel == 0 || j >= q.n_c) return;
+  const uint8_t* Hj = hcol(q, j);
+  unsigned long long* rmask = rmcol(q, j);
+  uint32_t* rlist = rlcol(q, j);
+  uint32_t* ovf = s.rcnt + size_t(j) * kRecStride + (kMaxLevel + 2);
+  for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
+    const uint32_t v = uint32_t(c->sel_int[gi]);
+    if (j == 0) {                                  // the CG nodes themselves belong to V^c
+      const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
+      if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+    }
+    if (Hj[v] == 0) continue;                      // the CG node holds keyword j
+    if (atomicOr(&rmask[v], 1ull << gi) == 0) rec_overflow(c, rlist, ovf, s.cap, v);
+  }
+}
+
+// Level x of column j's sweep, the share of CTA `rank` of the R CTAs on the
+// column: every CTA scans the level's entries (segment of level x from
+// entry `base`, then the overflow nodes with h = x), and the CSR entries
+// with a <= x-1 of those nodes are dealt round-robin over the R CTAs.
+// s_off and s_rb hold blockDim.x entries, s_m as many.
+__device__ void rec_level(const DevKG& g, const DevSlot& s, int j, uint32_t rank, uint32_t R, int x, uint32_t base,
+                          uint32_t* s_off, uint32_t* s_rb, unsigned long long* s_m) {
+  Ctl* c = s.ctl;
+  const QueryDev& q = *s.q;
   const uint32_t cap = s.cap;
   const uint8_t* Hj = hcol(q, j);
   unsigned long long* rmask = rmcol(q, j);
   uint32_t* rlist = rlcol(q, j);
   uint32_t* sn = s.rcnt + size_t(j) * kRecStride;          // sn[y]: segment length of level y
   uint32_t* ovf = sn + (kMaxLevel + 2);                    // overflow length
-  __shared__ uint32_t s_off[kRecThreads];
-  __shared__ uint32_t s_rb[kRecThreads];
-  __shared__ unsigned long long s_m[kRecThreads];
   __shared__ uint64_t s_warp[33];
-  __shared__ uint32_t s_total;
-  auto to_overflow = [&](uint32_t v) {
-    const uint32_t p = atomicAdd(ovf, 1u);
-    if (p < cap) rlist[cap - 1u - p] = v; else atomicOr(&c->err, kErrOverflow);
-  };
-  if (rank == 0) {
-    for (uint32_t gi = threadIdx.x; gi < nsel; gi += blockDim.x) {
-      const uint32_t v = uint32_t(c->sel_int[gi]);
-      if (j == 0) {                                  // the CG nodes themselves belong to V^c
-        const unsigned long long old = atomicOr(&s.vmask[v], 1ull << gi);
-        if (old == 0) s.ulist[atomicAdd(&c->ulist_n, 1u)] = v;
+  __shared__ uint32_t s_total, s_cnt[2];
+  const uint32_t stride = R * blockDim.x;
+  // one read for the whole block: other CTAs append to the overflow while
+  // this level runs, and every thread must run the same rounds (barriers)
+  if (threadIdx.x == 0) { s_cnt[0] = __ldcg(&sn[x]); s_cnt[1] = min(__ldcg(ovf), cap); }
+  __syncthreads();
+  const uint32_t nseg = s_cnt[0], nov = s_cnt[1];
+  const uint32_t next_base = base + nseg, cnt = nseg + nov;
+  for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
+    const uint32_t i = c0 + threadIdx.x;
+    uint32_t len = 0, rb = 0;
+    unsigned long long m = 0;
+    if (i < cnt) {
+      const uint32_t qn = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
+      // every load of the node first (the addresses depend on qn alone)
+      const uint32_t hq = Hj[qn];
+      const uint32_t r0 = g.row_ptr[qn], r1 = g.row_ptr[qn + 1];
+      const uint32_t o = uint32_t(x) <= kLvxLevels ? g.lvx[size_t(x - 1) * size_t(g.n) + qn] : 0u;
+      const unsigned long long mq = __ldcg(rmask + qn);
+      if (i < nseg || hq == uint32_t(x)) {
+        uint32_t hi;                               // first entry with a >= x
+        if (uint32_t(x) > kLvxLevels) hi = seg_lower(g.adj, r0, r1, uint32_t(x));
+        else if (r1 - r0 <= kLvxMaxDeg) hi = r0 + o;
+        else hi = r0 + g.lvx_long[size_t(o) * kLvxLevels + (x - 1)];
+        rb = r0;
+        len = hi - r0;                             // edges with a <= x-1
+        m = mq;
       }
-      if (Hj[v] == 0) continue;                      // the CG node holds keyword j
-      if (atomicOr(&rmask[v], 1ull << gi) == 0) to_overflow(v);
     }
-  }
-  cluster.sync();
-  const uint32_t stride = kRecCluster * blockDim.x;
-  uint32_t base = 0;                                 // first entry of the segment of level x
-  for (int x = maxlev; x >= 1; --x) {
-    const uint32_t nseg = __ldcg(&sn[x]), nov = min(__ldcg(ovf), cap);
-    const uint32_t next_base = base + nseg, cnt = nseg + nov;
-    for (uint32_t c0 = 0; c0 < cnt; c0 += blockDim.x) {
-      const uint32_t i = c0 + threadIdx.x;
-      uint32_t len = 0, rb = 0;
-      unsigned long long m = 0;
-      if (i < cnt) {
-        const uint32_t qn = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
-        // every load of the node first (the addresses depend on qn alone)
-        const uint32_t hq = Hj[qn];
-        const uint32_t r0 = g.row_ptr[qn], r1 = g.row_ptr[qn + 1];
-        const uint32_t o = uint32_t(x) <= kLvxLevels ? g.lvx[size_t(x - 1) * size_t(g.n) + qn] : 0u;
-        const unsigned long long mq = __ldcg(rmask + qn);
-        if (i < nseg || hq == uint32_t(x)) {
-          uint32_t hi;                               // first entry with a >= x
-          if (uint32_t(x) > kLvxLevels) hi = seg_lower(g.adj, r0, r1, uint32_t(x));
-          else if (r1 - r0 <= kLvxMaxDeg) hi = r0 + o;
-          else hi = r0 + g.lvx_long[size_t(o) * kLvxLevels + (x - 1)];
-          rb = r0;
-          len = hi - r0;                             // edges with a <= x-1
-          m = mq;
-        }
+    uint64_t tot = 0;
+    const uint32_t pre = uint32_t(block_excl_scan(len, s_warp, &tot));
+    s_off[threadIdx.x] = pre; s_rb[threadIdx.x] = rb; s_m[threadIdx.x] = m;
+    if (threadIdx.x == 0) s_total = uint32_t(tot);
+    __syncthreads();
+    const uint32_t total = s_total;
+    for (uint32_t u = rank * blockDim.x + threadIdx.x; u < total; u += stride) {
+      uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u
+      while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo + 1) >> 1);
+        if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
       }
-      uint64_t tot = 0;
-      const uint32_t pre = uint32_t(block_excl_scan(len, s_warp, &tot));
-      s_off[threadIdx.x] = pre; s_rb[threadIdx.x] = rb; s_m[threadIdx.x] = m;
-      if (threadIdx.x == 0) s_total = uint32_t(tot);
-      __syncthreads();
-      const uint32_t total = s_total;
-      for (uint32_t u = rank * blockDim.x + threadIdx.x; u < total; u += stride) {
-        uint32_t lo = 0, hi = blockDim.x - 1;       // last slot with s_off <= u
-        while (lo < hi) {
-          const uint32_t mid = lo + ((hi - lo + 1) >> 1);
-          if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
-        const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
-        // all loads of the neighbour at once, then the tests
-        const uint32_t vb = vis_byte(s.vis, nb), hn = Hj[nb], cfw = s.cf[nb >> 5], stl = s.stopl[nb];
-        if (!((vb >> j) & 1u)) continue;
-        const uint32_t lam = a > hn ? a : hn;
-        if (lam + 1 != uint32_t(x)) continue;                               // not tight
-        if (((cfw >> (nb & 31u)) & 1u) && stl <= lam) continue;             // nb had stopped
-        if (atomicOr(&rmask[nb], s_m[lo]) != 0) continue;                  // already listed
-        if (hn + 1 == uint32_t(x)) {
-          const uint32_t p = next_base + atomicAdd(&sn[hn], 1u);
-          if (p < cap) rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
-        } else {
-          to_overflow(nb);
-        }
+      const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
+      const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
+      // all loads of the neighbour at once, then the tests
+      const uint32_t vb = vis_byte(s.vis, nb), hn = Hj[nb], cfw = s.cf[nb >> 5], stl = s.stopl[nb];
+      if (!((vb >> j) & 1u)) continue;
+      const uint32_t lam = a > hn ? a : hn;
+      if (lam + 1 != uint32_t(x)) continue;                               // not tight
+      if (((cfw >> (nb & 31u)) & 1u) && stl <= lam) continue;             // nb had stopped
+      if (atomicOr(&rmask[nb], s_m[lo]) != 0) continue;                  // already listed
+      if (hn + 1 == uint32_t(x)) {
+        const uint32_t p = next_base + atomicAdd(&sn[hn], 1u);
+        if (p < cap) rlist[p] = nb; else atomicOr(&c->err, kErrOverflow);
+      } else {
+        rec_overflow(c, rlist, ovf, cap, nb);
       }
-      __syncthreads();
     }
-    cluster.sync();                                  // level x done everywhere before level x-1
-    base = next_base;
+    __syncthreads();
   }
-  // every reached node: a keyword holder's column mask goes into the union
-  // mask; the column mask is cleared
-  const uint32_t nseg = base + __ldcg(&sn[0]), nov = min(__ldcg(ovf), cap);
+}
+
+// End of column j's sweep (CTA `rank` of R, after its last level; `nseg`
+// entries in the level segments): every reached node that holds a central
+// keyword ORs its column mask into the union mask (vmask), and every column
+// mask is cleared.  The last CTA of all columns (n_c * R of them) keeps the
+// nodes of V^c that hold a central keyword: V_C of each CG, as
+// (g << 26 | node) pairs; it also clears the list counters.
+__device__ void rec_finish(const DevSlot& s, int j, uint32_t rank, uint32_t R, uint32_t nseg) {
+  Ctl* c = s.ctl;
+  const QueryDev& q = *s.q;
+  const uint32_t cap = s.cap;
+  unsigned long long* rmask = rmcol(q, j);
+  const uint32_t* rlist = rlcol(q, j);
+  const uint32_t* ovf = s.rcnt + size_t(j) * kRecStride + (kMaxLevel + 2);
+  const uint32_t stride = R * blockDim.x;
+  const uint32_t nov = min(__ldcg(ovf), cap);
   for (uint32_t i = rank * blockDim.x + threadIdx.x; i < nseg + nov; i += stride) {
     const uint32_t v = i < nseg ? __ldcg(rlist + i) : __ldcg(rlist + cap - 1u - (i - nseg));
     const unsigned long long m = __ldcg(rmask + v);
@@ -1267,14 +1362,11 @@ k_recover_cols(DevKG g, DevSlot s) {
       if (p < cap) s.ulist[p] = v; else atomicOr(&c->err, kErrOverflow);
     }
   }
-  // the last CTA of all columns keeps the nodes of V^c that hold a central
-  // keyword: V_C of each CG, as (g << 26 | node) pairs; it also clears the
-  // list counters
   __shared__ uint32_t s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&c->rec_done, 1u) == uint32_t(q.n_c) * kRecCluster - 1u ? 1u : 0u;
+    s_last = atomicAdd(&c->rec_done, 1u) == uint32_t(q.n_c) * R - 1u ? 1u : 0u;
   }
   __syncthreads();
   if (!s_last) return;
@@ -1293,6 +1385,28 @@ k_recover_cols(DevKG g, DevSlot s) {
     }
   }
   if (threadIdx.x == 0) c->rec_done = 0;
+}
+
+__global__ void __cluster_dims__(kRecCluster, 1, 1) __launch_bounds__(kRecThreads, 1)
+k_recover_cols(DevKG g, DevSlot s) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int j = int(blockIdx.x / kRecCluster);
+  const uint32_t rank = cluster.block_rank();
+  if (s.ctl->nsel == 0 || j >= s.q->n_c) return;           // the same in every CTA of the cluster
+  __shared__ uint32_t s_off[kRecThreads];
+  __shared__ uint32_t s_rb[kRecThreads];
+  __shared__ unsigned long long s_m[kRecThreads];
+  if (rank == 0) rec_start(s, j);
+  cluster.sync();
+  const int maxlev = s.ctl->levels[0];
+  uint32_t base = 0;                                 // first entry of the segment of level x
+  for (int x = maxlev; x >= 1; --x) {
+    const uint32_t nseg = __ldcg(&s.rcnt[size_t(j) * kRecStride + x]);
+    rec_level(g, s, j, rank, kRecCluster, x, base, s_off, s_rb, s_m);
+    cluster.sync();                                  // level x done everywhere before level x-1
+    base += nseg;
+  }
+  rec_finish(s, j, rank, kRecCluster, base + __ldcg(&s.rcnt[size_t(j) * kRecStride]));
 }
 
 // --------------------------------------------------------------- results
@@ -1359,6 +1473,322 @@ __device__ void write_results(const DevSlot& s) {
 // there is no marginal run, else the k_expand that stops the marginal run).
 __global__ void k_results(DevSlot s) { write_results(s); }
 
+// ------------------------------------------ multi-query persistent kernel
+// A batch of queries runs in one launch of k_batch, one wave of blocks that
+// stay resident until the batch is done, over a device work queue: every
+// slot (the state of one query in flight) offers the chunks of its query's
+// current phase, a block takes one chunk with an atomic add on the slot's
+// phase word and runs it (the same device code as the launched kernels, with
+// the chunk as its block of the phase), and the block that finishes the
+// phase's last chunk computes the next phase and publishes it; a slot whose
+// query ends writes the query's record and takes the next query of the
+// batch.  The phase boundaries take the place of the kernel boundaries of
+// the launched sequence (release: fence, then the atomic that counts the
+// chunk done; acquire: the atomic that takes a chunk, then a fence), and a
+// phase has as many chunks as its work needs (one for a small frontier),
+// so small levels of some queries leave the other blocks to the dense
+// levels of others.  Recovery runs one phase per level of the sweep, in
+// place of the cluster barrier between levels.  Blocks never wait for one
+// another inside a phase; a block without work polls the slots, and a
+// watchdog ends the kernel (kErrTimeout) when no phase finishes for `limit`
+// clock cycles.
+constexpr int kBatchThreads = 256;
+constexpr int kBatchTopkChunk = 1024;
+constexpr uint32_t kBatchRec = kRecCluster;   // chunks per central column of a recovery phase
+static_assert(sizeof(rpq_result) == 24, "batch record layout");
+
+enum BatchPhase : uint32_t {
+  kPhClear = 1,      // zero the run's visited bytes and bit maps
+  kPhSeed,           // k_seed
+  kPhEnqueue,        // k_enqueue
+  kPhTarget,         // k_target
+  kPhExpand,         // k_expand
+  kPhTopk,           // k_topk
+  kPhRecStart,       // recovery: start of each column's sweep
+  kPhRecLevel,       // recovery: one level of every column's sweep
+  kPhRecFinish,      // recovery: union masks and V_C
+};
+
+struct BatchArgs {
+  DevKG g;
+  const QueryDev* queries;   // n_queries records (keyword ids and parameters)
+  uint8_t* out;              // kBatchRecBytes per query
+  BatchSlotState* bs;        // n_slots
+  BatchCtl* bc;
+  uint32_t n_queries, n_slots, n_sm;
+  long long limit;
+  DevSlot slot[kBatchMaxSlots];
+};
+
+__device__ __forceinline__ uint32_t clamp_chunks(uint64_t want, uint32_t most) {
+  return uint32_t(want < 1 ? 1 : (want > most ? most : want));
+}
+
+// Thread 0: the slot's next phase; its chunks are handed out from here on.
+__device__ __forceinline__ void batch_publish(BatchSlotState* b, BatchCtl* bc, uint32_t phase, uint32_t run,
+                                              uint32_t level, uint32_t nch) {
+  b->done = 0;
+  b->phase = phase;
+  b->run = run;
+  b->level = level;
+  __threadfence();
+  atomicExch(&b->word, (unsigned long long)nch << 32);
+  atomicAdd(&bc->progress, 1ull);
+}
+
+// Chunks of the phases whose size is known from the control block.
+__device__ uint32_t clear_chunks(const DevSlot& s, uint32_t grid) {
+  return clamp_chunks((s.run_clear_bytes + 65535ull) >> 16, grid);
+}
+__device__ uint32_t seed_chunks(const DevKG& g, const DevSlot& s, int run, uint32_t most) {
+  const QueryDev& q = *s.q;
+  const int nt = run == 0 ? q.n_c : q.n_m, kb = run == 0 ? 0 : q.n_c;
+  uint64_t total = 0;
+  for (int j = 0; j < nt; ++j) {
+    const int32_t kw = q.kw[kb + j];
+    if (kw >= 0 && kw < g.n_kw) total += g.kw_ptr[kw + 1] - g.kw_ptr[kw];
+  }
+  return clamp_chunks((total + kBatchThreads - 1) / kBatchThreads, most);
+}
+__device__ uint32_t enqueue_chunks(const DevKG& g, const DevSlot& s, uint32_t grid) {
+  const Ctl* c = s.ctl;
+  const int p = int(__ldcg(&c->lvl_enq) & 1u);
+  if (enqueue_sparse<true>(s, c, p)) return clamp_chunks((uint64_t(__ldcg(&c->fq_n[p])) + kEnqThreads - 1) / kEnqThreads, grid);
+  const uint64_t slots = uint64_t((uint32_t(g.n) + 31u) >> 5) * 32u;
+  return clamp_chunks((slots + kEnqThreads * kEnqRounds - 1) / (kEnqThreads * kEnqRounds), grid);
+}
+__device__ uint32_t expand_chunks(const DevSlot& s, int run, uint32_t grid) {
+  const LevelPlan plan = level_plan<true>(s, run, __ldcg(&s.ctl->lvl_exp));
+  if (plan.stop) return grid;                               // every block counts hits
+  if (plan.skip || plan.n_work == 0) return 1;              // the bookkeeping of block 0 only
+  const uint64_t tiles = (uint64_t(plan.n_work) + kWarpTile - 1) / kWarpTile;
+  return clamp_chunks((tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32), grid);
+}
+
+// Thread 0: the first query of the batch not yet started goes to slot sl
+// (k_set_query's work, with the slot's own columns), or the slot retires.
+__device__ void batch_start_query(const BatchArgs& a, uint32_t sl) {
+  BatchSlotState* b = a.bs + sl;
+  const uint32_t qi = atomicAdd(&a.bc->next_query, 1u);
+  if (qi >= a.n_queries) {
+    b->query = -1;
+    atomicExch(&b->word, 0ull);
+    return;
+  }
+  const DevSlot& s = a.slot[sl];
+  QueryDev* q = s.q;
+  *q = a.queries[qi];
+  for (int j = 0; j < kMaxCols; ++j) {
+    q->hc[j] = s.H + size_t(j) * s.hp;
+    q->rm[j] = s.rmask + size_t(j) * s.cap;
+    q->rl[j] = s.rlist + size_t(j) * s.cap;
+  }
+  Ctl* c = s.ctl;
+  uint32_t* w = reinterpret_cast<uint32_t*>(c);
+  for (size_t i = 0; i < sizeof(Ctl) / 4; ++i) w[i] = 0;
+  c->levels[0] = c->levels[1] = -1;
+  c->last_expanded = -1;
+  c->fq_use[0] = 1;
+  s.bar[0] = 0;
+  *s.n_res = 0;
+  b->query = int32_t(qi);
+  batch_publish(b, a.bc, kPhClear, 0, 0, clear_chunks(s, gridDim.x));
+}
+
+// k_run_start's work for the marginal run (thread 0).
+__device__ void batch_run_start(const DevSlot& s) {
+  Ctl* c = s.ctl;
+  c->done = (s.q->n_m == 0 || c->nsel == 0) ? 1u : 0u;
+  c->work[0] = c->work[1] = 0;
+  c->nq[0] = c->nq[1] = 0;
+  c->fq_n[0] = c->fq_n[1] = 0;
+  c->fq_over[0] = c->fq_over[1] = 0;
+  c->fq_use[0] = 1;
+  c->fq_use[1] = 0;
+  c->lvl_enq = c->lvl_exp = 0;
+  c->level = 0;
+  c->eact_lvl[0] = c->eact_lvl[1] = 0;
+  c->skip_lvl = 0;
+  c->ncg_at = 0;
+  c->cg_next[0] = c->cg_next[1] = 0;
+  c->tgt_n = c->tgt_done = 0;
+  s.bar[0] = 0;
+  c->last_expanded = -1;
+}
+
+// One chunk of the slot's current phase (every thread of the block).
+__device__ void batch_chunk(const BatchArgs& a, const DevSlot& s, uint32_t phase, uint32_t run, uint32_t level,
+                            Part pt, uint32_t* buf) {
+  const DevKG& g = a.g;
+  switch (phase) {
+    case kPhClear: {
+      uint4* p = static_cast<uint4*>(s.run_clear);
+      const unsigned long long n16 = s.run_clear_bytes >> 4;
+      const unsigned long long b0 = n16 * pt.b / pt.n, b1 = n16 * (pt.b + 1) / pt.n;
+      for (unsigned long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
+      break;
+    }
+    case kPhSeed: seed_body(g, s, int(run), pt); break;
+    case kPhEnqueue: enqueue_body<true>(g, s, int(run), pt); break;
+    case kPhTarget: target_body(g, s, pt); break;
+    case kPhExpand: expand_body<true>(g, s, int(run), 0, 0, pt); break;
+    case kPhTopk: topk_body<kBatchThreads, kBatchTopkChunk>(g, s, pt, buf, buf + kBatchTopkChunk + 2 * kMaxK); break;
+    case kPhRecStart: rec_start(s, int(pt.b)); break;
+    case kPhRecLevel:
+    case kPhRecFinish: {
+      const int j = int(pt.b / kBatchRec);
+      const uint32_t rank = pt.b % kBatchRec;
+      if (s.ctl->nsel == 0 || j >= s.q->n_c) break;
+      const int maxlev = s.ctl->levels[0];
+      const uint32_t* sn = s.rcnt + size_t(j) * kRecStride;
+      if (phase == kPhRecLevel) {
+        uint32_t base = 0;                          // the segments of the levels above
+        for (int y = maxlev; y > int(level); --y) base += __ldcg(&sn[y]);
+        rec_level(g, s, j, rank, kBatchRec, int(level), base, buf, buf + kBatchThreads,
+                  reinterpret_cast<unsigned long long*>(buf + 2 * kBatchThreads));
+      } else {
+        uint32_t nseg = 0;
+        for (int y = maxlev; y >= 0; --y) nseg += __ldcg(&sn[y]);
+        rec_finish(s, j, rank, kBatchRec, nseg);
+      }
+      break;
+    }
+    default: break;
+  }
+}
+
+// The block that finished the slot's phase: the next phase, or the end of
+// the query (its record, then the next query).  Every thread calls it.
+__device__ void batch_advance(const BatchArgs& a, uint32_t sl) {
+  BatchSlotState* b = a.bs + sl;
+  const DevSlot& s = a.slot[sl];
+  Ctl* c = s.ctl;
+  const uint32_t grid = gridDim.x, small = 2u * a.n_sm;
+  __shared__ uint32_t s_end;
+  if (threadIdx.x == 0) {
+    const uint32_t phase = __ldcg(&b->phase), run = __ldcg(&b->run), level = __ldcg(&b->level);
+    const QueryDev& q = *s.q;
+    bool end = false;
+    switch (phase) {
+      case kPhClear: batch_publish(b, a.bc, kPhSeed, run, 0, seed_chunks(a.g, s, int(run), small)); break;
+      case kPhSeed: batch_publish(b, a.bc, kPhEnqueue, run, 0, enqueue_chunks(a.g, s, grid)); break;
+      case kPhEnqueue:
+        if (run == 1 && target_runs<true>(s)) {
+          const uint32_t ntask = min(__ldcg(&c->nvc), s.cap) * uint32_t(q.n_m);
+          batch_publish(b, a.bc, kPhTarget, run, 0, clamp_chunks((ntask + 7u) / 8u, small));
+        } else {
+          batch_publish(b, a.bc, kPhExpand, run, 0, expand_chunks(s, int(run), grid));
+        }
+        break;
+      case kPhTarget: batch_publish(b, a.bc, kPhExpand, run, 0, expand_chunks(s, int(run), grid)); break;
+      case kPhExpand:
+        if (!__ldcg(&c->done) && __ldcg(&c->lvl_enq) <= uint32_t(q.L)) {
+          batch_publish(b, a.bc, kPhEnqueue, run, 0, enqueue_chunks(a.g, s, grid));
+        } else if (run == 0) {
+          const uint32_t n_in = min(__ldcg(&c->ncg), s.cap);
+          batch_publish(b, a.bc, kPhTopk, 0, 0, clamp_chunks((n_in + kBatchTopkChunk - 1) / kBatchTopkChunk, small));
+        } else {
+          end = true;
+        }
+        break;
+      case kPhTopk:
+        if (q.n_m == 0 || __ldcg(&c->nsel) == 0) end = true;   // k_topk wrote the results
+        else batch_publish(b, a.bc, kPhRecStart, 0, 0, uint32_t(q.n_c));
+        break;
+      case kPhRecStart:
+      case kPhRecLevel: {
+        const int next = phase == kPhRecStart ? __ldcg(&c->levels[0]) : int(level) - 1;
+        if (next >= 1) batch_publish(b, a.bc, kPhRecLevel, 0, uint32_t(next), uint32_t(q.n_c) * kBatchRec);
+        else batch_publish(b, a.bc, kPhRecFinish, 0, 0, uint32_t(q.n_c) * kBatchRec);
+        break;
+      }
+      case kPhRecFinish:
+        batch_run_start(s);
+        if (c->done) end = true;
+        else batch_publish(b, a.bc, kPhClear, 1, 0, clear_chunks(s, grid));
+        break;
+      default: end = true; break;
+    }
+    s_end = end ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_end) return;
+  // the query's record: control block and results, then the flag
+  const int32_t qi = __ldcg(&b->query);
+  uint32_t* rec = reinterpret_cast<uint32_t*>(a.out + size_t(qi) * kBatchRecBytes);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(c);            // the results follow the control block
+  for (uint32_t i = threadIdx.x; i < (kCtlBytes + 24 * kMaxK) / 4; i += blockDim.x) rec[kBatchRecHead / 4 + i] = __ldcg(src + i);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    rec[0] = 1u;
+    __threadfence();
+    atomicAdd(&a.bc->finished, 1u);
+    batch_start_query(a, sl);
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 6)
+k_batch(const __grid_constant__ BatchArgs a) {
+  __shared__ __align__(16) uint32_t buf[kBatchTopkChunk + 2 * kMaxK + 2048];   // top-w keys + histogram, or recovery scan
+  __shared__ int s_slot;
+  __shared__ uint32_t s_chunk, s_nch, s_phase, s_run, s_level, s_exit, s_last;
+  if (blockIdx.x < a.n_slots && threadIdx.x == 0) batch_start_query(a, blockIdx.x);
+  uint32_t start = blockIdx.x % a.n_slots;         // thread 0: first slot it polls
+  unsigned long long seen = ~0ull;                 // thread 0: progress count last seen, and when
+  long long since = clock64();
+  for (;;) {
+    __syncthreads();                               // every thread has read the last round's shared values
+    if (threadIdx.x == 0) {
+      int got = -1;
+      // after a watchdog timeout no block takes further work
+      const bool stopped = *(volatile uint32_t*)&a.bc->err != 0;
+      for (uint32_t t = 0; t < a.n_slots && got < 0 && !stopped; ++t) {
+        uint32_t sl = start + t;
+        if (sl >= a.n_slots) sl -= a.n_slots;
+        const unsigned long long w = *(volatile unsigned long long*)&a.bs[sl].word;
+        if (uint32_t(w) >= uint32_t(w >> 32)) continue;
+        const unsigned long long o = atomicAdd(&a.bs[sl].word, 1ull);
+        if (uint32_t(o) < uint32_t(o >> 32)) {
+          got = int(sl);
+          s_chunk = uint32_t(o);
+          s_nch = uint32_t(o >> 32);
+        }
+      }
+      s_exit = 0;
+      if (got >= 0) {
+        __threadfence();                           // acquire: the phase's inputs
+        const BatchSlotState* b = a.bs + got;
+        s_phase = __ldcg(&b->phase); s_run = __ldcg(&b->run); s_level = __ldcg(&b->level);
+        start = uint32_t(got);
+      } else if (stopped || *(volatile uint32_t*)&a.bc->finished >= a.n_queries) {
+        s_exit = 1;
+      } else {
+        const unsigned long long pr = *(volatile unsigned long long*)&a.bc->progress;
+        const long long now = clock64();
+        if (pr != seen) { seen = pr; since = now; }
+        else if (now - since > a.limit) { atomicOr(&a.bc->err, kErrTimeout); s_exit = 1; }
+        else __nanosleep(256);
+      }
+      s_slot = got;
+    }
+    __syncthreads();
+    if (s_exit) break;
+    const int sl = s_slot;
+    if (sl < 0) continue;
+    const uint32_t nch = s_nch;
+    batch_chunk(a, a.slot[sl], s_phase, s_run, s_level, Part{s_chunk, nch}, buf);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();                             // release: this chunk's writes
+      s_last = atomicAdd(&a.bs[sl].done, 1u) == nch - 1u ? 1u : 0u;
+      if (s_last) __threadfence();                 // acquire: every chunk's writes
+    }
+    __syncthreads();
+    if (s_last) batch_advance(a, uint32_t(sl));
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launchers
@@ -1408,6 +1838,29 @@ static int one_wave_grid(K kernel, int threads) {
     per_sm = 1;
   }
   return num_sms() * per_sm;
+}
+
+size_t batch_state_bytes(int n_slots) { return sizeof(BatchSlotState) * size_t(n_slots) + sizeof(BatchCtl); }
+
+int launch_batch(const DevKG& g, const DevSlot* slots, int n_slots, const QueryDev* d_queries, int n_queries,
+                 void* d_out, void* d_state, long long limit, cudaStream_t st) {
+  if (n_slots < 1 || n_slots > kBatchMaxSlots || n_queries < 1) return RPQ_EINVAL;
+  static const int grid = one_wave_grid(k_batch, kBatchThreads);
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = g;
+  a.queries = d_queries;
+  a.out = static_cast<uint8_t*>(d_out);
+  a.bs = static_cast<BatchSlotState*>(d_state);
+  a.bc = reinterpret_cast<BatchCtl*>(a.bs + n_slots);
+  a.n_queries = uint32_t(n_queries);
+  a.n_slots = uint32_t(n_slots);
+  a.n_sm = uint32_t(num_sms());
+  a.limit = limit;
+  for (int i = 0; i < n_slots; ++i) a.slot[i] = slots[i];
+  if (cudaMemsetAsync(d_state, 0, batch_state_bytes(n_slots), st) != cudaSuccess) return RPQ_ECUDA;
+  k_batch<<<grid, kBatchThreads, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? RPQ_OK : RPQ_ECUDA;
 }
 
 // One run as a single cooperative launch of k_run (one wave of blocks).
