@@ -559,6 +559,13 @@ def batched_mix(args, ws, ds, kg):
     t0 = time.perf_counter()
     out = kg.search_batch(mq)
     t_b = allmax(ws, time.perf_counter() - t0)
+    pers = kg.search_batch(mq, persistent=True)                 # warm-up and results
+    barrier(ws)
+    t0 = time.perf_counter()
+    pers = kg.search_batch(mq, persistent=True)
+    t_p = allmax(ws, time.perf_counter() - t0)
+    for i, ((b, _, _), (p, _, st)) in enumerate(zip(out, pers)):
+        assert st == 0 and p.tobytes() == b.tobytes(), f"persistent-batch result differs on mix query {i}"
     barrier(ws)
     t0 = time.perf_counter()
     one = [kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)[0] for q in mq]
@@ -566,7 +573,8 @@ def batched_mix(args, ws, ds, kg):
     for i, (r, (b, _, _)) in enumerate(zip(one, out)):
         assert r.tobytes() == b.tobytes(), f"batched result differs from one-at-a-time on mix query {i}"
     return {"queries_per_call": len(mq), "batched_qps": ws * len(mq) / t_b, "one_at_a_time_qps": ws * len(mq) / t_1,
-            "batched_vs_one_at_a_time": t_1 / t_b, "equal_results_checked": len(mq),
+            "batched_vs_one_at_a_time": t_1 / t_b, "persistent_batch_qps": ws * len(mq) / t_p,
+            "persistent_vs_slots": t_b / t_p, "equal_results_checked": len(mq),
             "e_act": sum(st["e_act_central"] + st["e_act_marginal"] for _, st, _ in out),
             "queries": mq, "results": one}
 
@@ -575,7 +583,8 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
     """All queries in one rpq_search_batch call per step; a sample is also run
     one at a time and must give identical results."""
     nq = len(qs)
-    res0 = kg.search_batch(qs)
+    pers = args.batch_form == "persistent"
+    res0 = kg.search_batch(qs, persistent=pers)
     assert all(st == 0 for _, _, st in res0), "batch query failed"
     sample = list(range(0, nq, max(1, nq // 128)))
     t0 = time.perf_counter()
@@ -584,16 +593,22 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
         assert r.tobytes() == res0[i][0].tobytes(), f"batched result differs from one-at-a-time on query {i}"
     one_qps = len(sample) / (time.perf_counter() - t0)
     for _ in range(max(0, args.warmup - 1)):
-        kg.search_batch(qs)
+        kg.search_batch(qs, persistent=pers)
     clocks = Clocks(local)
     barrier(ws)
     clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        out = kg.search_batch(qs)
+        out = kg.search_batch(qs, persistent=pers)
     t = allmax(ws, time.perf_counter() - t0)
     clk = clocks.stop()
     value = ws * nq * args.steps / t
+    # the other batch form, one pass on the same queries (same results)
+    t0 = time.perf_counter()
+    other = kg.search_batch(qs, persistent=not pers)
+    t_other = allmax(ws, time.perf_counter() - t0)
+    for i, ((a, _, _), (b, _, st)) in enumerate(zip(out, other)):
+        assert st == 0 and a.tobytes() == b.tobytes(), f"batch forms differ on query {i}"
     stats = [st for _, st, _ in out]
     e_act = sum(s["e_act_central"] + s["e_act_marginal"] for s in stats)
     sstats = [stats[i] for i in sample]
@@ -612,10 +627,12 @@ def run_batch(args, ws, rank, local, wl, ds, qs, kg):
         "gteps": e_act * ws * args.steps / t / 1e9,
         "one_at_a_time_qps": one_qps,
         "batched_vs_one_at_a_time": value / (ws * one_qps),
+        "batch_form": args.batch_form,
+        ("slots_qps" if pers else "persistent_qps"): ws * nq / t_other,
         "equal_results_checked": len(sample),
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": step_transfer_bytes(qs)[0],
                 "d2h_bytes_per_step": step_transfer_bytes(qs)[1]},
-        "gpu_launches": sum(s["kernels"] for s in stats) * args.steps,
+        "gpu_launches": (1 if pers else sum(s["kernels"] for s in stats)) * args.steps,   # persistent: one launch per step
         "roofline": roof, "kernel_ms_per_step_sample": kms,
         "oracle_checked": {"batched": len(idx)},
         "cpu_baseline": dict(cpu, sample=f"{len(idx)} of the {nq} queries (evenly spaced), serial C oracle, "
@@ -707,6 +724,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=-1,
                     help="queries the oracle checks (-1: every query on medium, one per host core on large)")
     ap.add_argument("--raks-cpu", type=int, default=1, help="time the paper's OpenMP CPU search on 8 queries")
+    ap.add_argument("--batch-form", default="slots", choices=["slots", "persistent"],
+                    help="batched workload: per-query graphs on concurrent slots, or the whole batch in one "
+                         "persistent kernel fed by a device work queue (the other form is timed once beside it)")
     ap.add_argument("--mix-queries", type=int, default=512,
                     help="large workload: queries of the batched mix run batched and one at a time")
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),

@@ -217,7 +217,7 @@ struct DevSlot {
 // slot to its next phase.
 constexpr int kBatchMaxSlots = 32;
 struct BatchSlotState {
-  unsigned long long word;   // (chunks of the current phase << 32) | next chunk to hand out
+  unsigned long long word;   // the current phase (search_kernels.cu: batch_word) and the next chunk to hand out
   uint32_t done;             // chunks of the current phase finished
   uint32_t phase;            // current phase (search_kernels.cu)
   uint32_t run;              // its run (0 central, 1 marginal)

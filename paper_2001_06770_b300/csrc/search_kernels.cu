@@ -64,6 +64,7 @@ constexpr int kRecThreads = 1024;
 constexpr int kRecCluster = 8;                     // CTAs sweeping one keyword column
 constexpr int kTopkThreads = 1024;
 constexpr int kTopkChunk = 4096;                   // keys per block and round of the top-w selection
+constexpr int kTopkBits = 11;                      // radix digit of the top-w selection
 constexpr unsigned long long kWorkBits = 38;
 constexpr unsigned long long kWorkMask = (1ull << kWorkBits) - 1ull;
 
@@ -79,8 +80,10 @@ __device__ __forceinline__ uint64_t block_sum(uint64_t v, uint64_t* s_warp) {
 }
 
 // Load of a value that other blocks may have written earlier in the same
-// kernel: in the persistent kernel (P) it must come from L2, not a possibly
-// stale L1 line; separate kernels may use the cached path.
+// kernel.  The persistent run kernel (P) reads such values from L2; separate
+// kernels, and the chunks of the multi-query persistent kernel (each taken
+// with an acquire: an atomic, then a fence, after the release of the phases
+// before it), use the cached path.
 template <bool P, typename T>
 __device__ __forceinline__ T ldx(const T* ptr) {
   if constexpr (P) return __ldcg(ptr);
@@ -286,8 +289,16 @@ __device__ __forceinline__ bool enqueue_sparse(const DevSlot& s, const Ctl* c, i
   return ldx<P>(&c->fq_use[p]) && !ldx<P>(&c->fq_over[p]) && ldx<P>(&c->fq_n[p]) <= s.fq_limit;
 }
 
+// Shared memory of the enqueue, declared once for every column count.
+struct EnqShared {
+  uint64_t warp[33];
+  unsigned long long base;
+  uint32_t acc[kMaxK];
+};
+
 template <bool P, int NT>
-__device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l, Part pt) {
+__device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, int run, uint32_t l, Part pt,
+                                              EnqShared& sh) {
   Ctl* c = s.ctl;
   const QueryDev& q = *s.q;
   constexpr int nt = NT;
@@ -296,9 +307,9 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
   const int p = int(l & 1u);
   uint32_t* Fc = s.F[p];
   uint32_t* Fn = s.F[p ^ 1];
-  __shared__ uint64_t s_warp[33];
-  __shared__ unsigned long long s_base;
-  __shared__ uint32_t s_acc[kMaxK];
+  uint64_t* s_warp = sh.warp;
+  unsigned long long& s_base = sh.base;
+  uint32_t* s_acc = sh.acc;
 
   if (run == 1 && pt.b == pt.n - 1u) {
     // RPG identification: a selected CG matches when every marginal keyword
@@ -552,15 +563,16 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
 template <bool P>
 __device__ __forceinline__ void enqueue_columns(const DevKG& g, const DevSlot& s, int run, uint32_t l, Part pt) {
   const QueryDev& q = *s.q;
+  __shared__ EnqShared sh;
   switch (run == 0 ? q.n_c : q.n_m) {
-    case 1: enqueue_level<P, 1>(g, s, run, l, pt); break;
-    case 2: enqueue_level<P, 2>(g, s, run, l, pt); break;
-    case 3: enqueue_level<P, 3>(g, s, run, l, pt); break;
-    case 4: enqueue_level<P, 4>(g, s, run, l, pt); break;
-    case 5: enqueue_level<P, 5>(g, s, run, l, pt); break;
-    case 6: enqueue_level<P, 6>(g, s, run, l, pt); break;
-    case 7: enqueue_level<P, 7>(g, s, run, l, pt); break;
-    default: enqueue_level<P, kMaxCols>(g, s, run, l, pt); break;
+    case 1: enqueue_level<P, 1>(g, s, run, l, pt, sh); break;
+    case 2: enqueue_level<P, 2>(g, s, run, l, pt, sh); break;
+    case 3: enqueue_level<P, 3>(g, s, run, l, pt, sh); break;
+    case 4: enqueue_level<P, 4>(g, s, run, l, pt, sh); break;
+    case 5: enqueue_level<P, 5>(g, s, run, l, pt, sh); break;
+    case 6: enqueue_level<P, 6>(g, s, run, l, pt, sh); break;
+    case 7: enqueue_level<P, 7>(g, s, run, l, pt, sh); break;
+    default: enqueue_level<P, kMaxCols>(g, s, run, l, pt, sh); break;
   }
 }
 
@@ -1051,8 +1063,10 @@ __device__ void block_key_range(const uint32_t* keys, uint32_t len, uint32_t* s_
 
 // The K-th smallest (1-based, K <= number of valid keys) of keys[0..len),
 // all of whose valid keys lie in [lo, lo + 2^span): a radix select over the
-// offsets from lo, most significant digits first, up to 11 bits per round
-// with a shared-memory histogram.  All threads of the block call it.
+// offsets from lo, most significant digits first, up to BITS bits per round
+// with a shared-memory histogram of 2^BITS bins.  All threads of the block
+// call it.
+template <int BITS>
 __device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K, uint32_t lo, uint32_t span,
                                   uint32_t* hist, uint64_t* s_warp, uint32_t* s_bin) {
   uint64_t prefix = 0;                                   // decided high bits of the offset
@@ -1060,7 +1074,7 @@ __device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K
   const uint32_t nt = blockDim.x;
 #pragma unroll 1
   for (uint32_t rem = span; rem > 0;) {
-    const uint32_t bits = min(rem, 11u), sh = rem - bits;
+    const uint32_t bits = min(rem, uint32_t(BITS)), sh = rem - bits;
     const uint32_t B = 1u << bits, per = (B + nt - 1) / nt;
     for (uint32_t i = threadIdx.x; i < B; i += nt) hist[i] = 0;
     __syncthreads();
@@ -1090,14 +1104,14 @@ __device__ uint32_t block_kth_key(const uint32_t* keys, uint32_t len, uint32_t K
 
 // Keep the (at most) K smallest valid keys of keys[0..len) in place; returns
 // their count.  len <= PER * blockDim.x.
-template <int PER>
+template <int PER, int BITS>
 __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K, uint32_t* hist,
                                         uint64_t* s_warp, uint32_t* s_bin, uint32_t* s_red) {
   if (threadIdx.x == 0) s_bin[3] = 0;
   uint32_t kmin, kmax, valid;
   block_key_range(keys, len, s_red, kmin, kmax, valid);   // ends with a barrier
   const uint32_t span = kmax > kmin ? 32u - uint32_t(__clz(kmax - kmin)) : 0u;
-  const uint32_t t = valid > K ? block_kth_key(keys, len, K, kmin, span, hist, s_warp, s_bin) : 0xfffffffeu;
+  const uint32_t t = valid > K ? block_kth_key<BITS>(keys, len, K, kmin, span, hist, s_warp, s_bin) : 0xfffffffeu;
   // compact keys <= t to the front (order is restored by the final ranking)
   uint32_t mine[PER];
   uint32_t nm = 0;
@@ -1109,8 +1123,8 @@ __device__ uint32_t block_keep_smallest(uint32_t* keys, uint32_t len, uint32_t K
   return min(valid, K);
 }
 
-// key holds CHUNK + 2 kMaxK entries and hist 2048; the block has NT threads.
-template <int NT, int CHUNK>
+// key holds CHUNK + 2 kMaxK entries and hist 2^BITS; the block has NT threads.
+template <int NT, int CHUNK, int BITS>
 __device__ void topk_body(const DevKG& g, const DevSlot& s, Part pt, uint32_t* key, uint32_t* hist) {
   constexpr int PER = CHUNK / NT;
   Ctl* c = s.ctl;
@@ -1129,12 +1143,12 @@ __device__ void topk_body(const DevKG& g, const DevSlot& s, Part pt, uint32_t* k
     const uint32_t len = min(uint32_t(CHUNK), n_in - b);
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) key[i] = s.cg[b + i];
     __syncthreads();
-    const uint32_t m = block_keep_smallest<PER>(key, len, K, hist, s_warp, s_bin, s_red);
+    const uint32_t m = block_keep_smallest<PER, BITS>(key, len, K, hist, s_warp, s_bin, s_red);
     // merge with the survivors of earlier chunks
     const uint32_t k0 = s_keep;
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) keep[k0 + i] = key[i];
     __syncthreads();
-    const uint32_t mm = block_keep_smallest<PER>(keep, k0 + m, K, hist, s_warp, s_bin, s_red);
+    const uint32_t mm = block_keep_smallest<PER, BITS>(keep, k0 + m, K, hist, s_warp, s_bin, s_red);
     if (threadIdx.x == 0) s_keep = mm;
     __syncthreads();
   }
@@ -1156,7 +1170,7 @@ __device__ void topk_body(const DevKG& g, const DevSlot& s, Part pt, uint32_t* k
     total += K;
     if (total + K > uint32_t(CHUNK) || blk + 1 == nb) {
       __syncthreads();
-      total = block_keep_smallest<PER>(key, total, K, hist, s_warp, s_bin, s_red);
+      total = block_keep_smallest<PER, BITS>(key, total, K, hist, s_warp, s_bin, s_red);
       __syncthreads();
     }
   }
@@ -1189,8 +1203,8 @@ __device__ void topk_body(const DevKG& g, const DevSlot& s, Part pt, uint32_t* k
 
 __global__ void __launch_bounds__(kTopkThreads) k_topk(DevKG g, DevSlot s) {
   __shared__ uint32_t key[kTopkChunk + 2 * kMaxK];
-  __shared__ uint32_t hist[2048];
-  topk_body<kTopkThreads, kTopkChunk>(g, s, launch_part(), key, hist);
+  __shared__ uint32_t hist[1 << kTopkBits];
+  topk_body<kTopkThreads, kTopkChunk, kTopkBits>(g, s, launch_part(), key, hist);
 }
 
 // ---------------------------------------------------------------- recovery
@@ -1479,8 +1493,9 @@ __global__ void k_results(DevSlot s) { write_results(s); }
 // slot (the state of one query in flight) offers the chunks of its query's
 // current phase, a block takes one chunk with an atomic add on the slot's
 // phase word and runs it (the same device code as the launched kernels, with
-// the chunk as its block of the phase), and the block that finishes the
-// phase's last chunk computes the next phase and publishes it; a slot whose
+// the chunk as its block of the phase; blocks prefer the oldest query with
+// chunks left), and the block that finishes the phase's last chunk computes
+// the next phase and publishes it; a slot whose
 // query ends writes the query's record and takes the next query of the
 // batch.  The phase boundaries take the place of the kernel boundaries of
 // the launched sequence (release: fence, then the atomic that counts the
@@ -1493,7 +1508,8 @@ __global__ void k_results(DevSlot s) { write_results(s); }
 // watchdog ends the kernel (kErrTimeout) when no phase finishes for `limit`
 // clock cycles.
 constexpr int kBatchThreads = 256;
-constexpr int kBatchTopkChunk = 1024;
+constexpr int kBatchTopkChunk = 512;               // top-w selection: keys per chunk round, radix digit
+constexpr int kBatchTopkBits = 8;
 constexpr uint32_t kBatchRec = kRecCluster;   // chunks per central column of a recovery phase
 static_assert(sizeof(rpq_result) == 24, "batch record layout");
 
@@ -1520,6 +1536,16 @@ struct BatchArgs {
   DevSlot slot[kBatchMaxSlots];
 };
 
+// A slot's phase word: next chunk to hand out (bits 0-23), chunks of the
+// phase (24-39), phase (40-43), run (44) and level (45-50), so that the
+// atomic add that takes a chunk also returns what the chunk is.  Blocks add
+// only after reading next < chunks, so next stays below chunks + blocks.
+__device__ __forceinline__ unsigned long long batch_word(uint32_t phase, uint32_t run, uint32_t level, uint32_t nch) {
+  return (uint64_t(level) << 45) | (uint64_t(run) << 44) | (uint64_t(phase) << 40) | (uint64_t(nch) << 24);
+}
+__device__ __forceinline__ uint32_t word_next(unsigned long long w) { return uint32_t(w) & 0xffffffu; }
+__device__ __forceinline__ uint32_t word_chunks(unsigned long long w) { return uint32_t(w >> 24) & 0xffffu; }
+
 __device__ __forceinline__ uint32_t clamp_chunks(uint64_t want, uint32_t most) {
   return uint32_t(want < 1 ? 1 : (want > most ? most : want));
 }
@@ -1532,11 +1558,15 @@ __device__ __forceinline__ void batch_publish(BatchSlotState* b, BatchCtl* bc, u
   b->run = run;
   b->level = level;
   __threadfence();
-  atomicExch(&b->word, (unsigned long long)nch << 32);
+  atomicExch(&b->word, batch_word(phase, run, level, nch));
   atomicAdd(&bc->progress, 1ull);
 }
 
-// Chunks of the phases whose size is known from the control block.
+// Chunks of the phases whose size is known from the control block, at most
+// one per block: at least two frontier-queue tiles, four bit-map tiles or
+// two warp tiles of work units per warp, so that the cost of taking a chunk
+// stays small against its work; a small level gets few chunks and leaves
+// the other blocks to other queries.
 __device__ uint32_t clear_chunks(const DevSlot& s, uint32_t grid) {
   return clamp_chunks((s.run_clear_bytes + 65535ull) >> 16, grid);
 }
@@ -1553,16 +1583,16 @@ __device__ uint32_t seed_chunks(const DevKG& g, const DevSlot& s, int run, uint3
 __device__ uint32_t enqueue_chunks(const DevKG& g, const DevSlot& s, uint32_t grid) {
   const Ctl* c = s.ctl;
   const int p = int(__ldcg(&c->lvl_enq) & 1u);
-  if (enqueue_sparse<true>(s, c, p)) return clamp_chunks((uint64_t(__ldcg(&c->fq_n[p])) + kEnqThreads - 1) / kEnqThreads, grid);
+  if (enqueue_sparse<true>(s, c, p)) return clamp_chunks((uint64_t(__ldcg(&c->fq_n[p])) + 2 * kEnqThreads - 1) / (2 * kEnqThreads), grid);
   const uint64_t slots = uint64_t((uint32_t(g.n) + 31u) >> 5) * 32u;
-  return clamp_chunks((slots + kEnqThreads * kEnqRounds - 1) / (kEnqThreads * kEnqRounds), grid);
+  return clamp_chunks((slots + 4 * kEnqThreads * kEnqRounds - 1) / (4 * kEnqThreads * kEnqRounds), grid);
 }
 __device__ uint32_t expand_chunks(const DevSlot& s, int run, uint32_t grid) {
   const LevelPlan plan = level_plan<true>(s, run, __ldcg(&s.ctl->lvl_exp));
   if (plan.stop) return grid;                               // every block counts hits
   if (plan.skip || plan.n_work == 0) return 1;              // the bookkeeping of block 0 only
   const uint64_t tiles = (uint64_t(plan.n_work) + kWarpTile - 1) / kWarpTile;
-  return clamp_chunks((tiles + kBatchThreads / 32 - 1) / (kBatchThreads / 32), grid);
+  return clamp_chunks((tiles + kBatchThreads / 16 - 1) / (kBatchThreads / 16), grid);
 }
 
 // Thread 0: the first query of the batch not yet started goes to slot sl
@@ -1629,10 +1659,12 @@ __device__ void batch_chunk(const BatchArgs& a, const DevSlot& s, uint32_t phase
       break;
     }
     case kPhSeed: seed_body(g, s, int(run), pt); break;
-    case kPhEnqueue: enqueue_body<true>(g, s, int(run), pt); break;
+    case kPhEnqueue: enqueue_body<false>(g, s, int(run), pt); break;
     case kPhTarget: target_body(g, s, pt); break;
-    case kPhExpand: expand_body<true>(g, s, int(run), 0, 0, pt); break;
-    case kPhTopk: topk_body<kBatchThreads, kBatchTopkChunk>(g, s, pt, buf, buf + kBatchTopkChunk + 2 * kMaxK); break;
+    case kPhExpand: expand_body<false>(g, s, int(run), 0, 0, pt); break;
+    case kPhTopk:
+      topk_body<kBatchThreads, kBatchTopkChunk, kBatchTopkBits>(g, s, pt, buf, buf + kBatchTopkChunk + 2 * kMaxK);
+      break;
     case kPhRecStart: rec_start(s, int(pt.b)); break;
     case kPhRecLevel:
     case kPhRecFinish: {
@@ -1730,37 +1762,49 @@ __device__ void batch_advance(const BatchArgs& a, uint32_t sl) {
 
 __global__ void __launch_bounds__(kBatchThreads, 6)
 k_batch(const __grid_constant__ BatchArgs a) {
-  __shared__ __align__(16) uint32_t buf[kBatchTopkChunk + 2 * kMaxK + 2048];   // top-w keys + histogram, or recovery scan
+  // scratch of the top-w selection (keys, histogram) or of a recovery level (scan)
+  constexpr int kBuf = kBatchTopkChunk + 2 * kMaxK + (1 << kBatchTopkBits) > 4 * kBatchThreads
+                       ? kBatchTopkChunk + 2 * kMaxK + (1 << kBatchTopkBits) : 4 * kBatchThreads;
+  __shared__ __align__(16) uint32_t buf[kBuf];
   __shared__ int s_slot;
   __shared__ uint32_t s_chunk, s_nch, s_phase, s_run, s_level, s_exit, s_last;
   if (blockIdx.x < a.n_slots && threadIdx.x == 0) batch_start_query(a, blockIdx.x);
-  uint32_t start = blockIdx.x % a.n_slots;         // thread 0: first slot it polls
-  unsigned long long seen = ~0ull;                 // thread 0: progress count last seen, and when
-  long long since = clock64();
+  // thread 0's watchdog state (progress count last seen, and when), kept in
+  // shared memory so that it holds no registers across the phase bodies
+  __shared__ unsigned long long seen;
+  __shared__ long long since;
+  if (threadIdx.x == 0) { seen = ~0ull; since = clock64(); }
   for (;;) {
     __syncthreads();                               // every thread has read the last round's shared values
     if (threadIdx.x == 0) {
       int got = -1;
       // after a watchdog timeout no block takes further work
       const bool stopped = *(volatile uint32_t*)&a.bc->err != 0;
-      for (uint32_t t = 0; t < a.n_slots && got < 0 && !stopped; ++t) {
-        uint32_t sl = start + t;
-        if (sl >= a.n_slots) sl -= a.n_slots;
-        const unsigned long long w = *(volatile unsigned long long*)&a.bs[sl].word;
-        if (uint32_t(w) >= uint32_t(w >> 32)) continue;
-        const unsigned long long o = atomicAdd(&a.bs[sl].word, 1ull);
-        if (uint32_t(o) < uint32_t(o >> 32)) {
-          got = int(sl);
-          s_chunk = uint32_t(o);
-          s_nch = uint32_t(o >> 32);
+      // oldest query first: every block takes a chunk of the oldest query
+      // with chunks left, so the blocks work on few queries at a time (their
+      // per-node state shares L2) and younger queries fill the gaps
+      for (int tries = 0; tries < 4 && got < 0 && !stopped; ++tries) {
+        int best = -1;
+        uint32_t best_q = 0xffffffffu;
+        for (uint32_t sl = 0; sl < a.n_slots; ++sl) {
+          const unsigned long long w = *(volatile unsigned long long*)&a.bs[sl].word;
+          const uint32_t qi = *(volatile uint32_t*)&a.bs[sl].query;
+          if (word_next(w) < word_chunks(w) && qi < best_q) { best = int(sl); best_q = qi; }
+        }
+        if (best < 0) break;
+        const unsigned long long o = atomicAdd(&a.bs[best].word, 1ull);
+        if (word_next(o) < word_chunks(o)) {
+          got = best;
+          s_chunk = word_next(o);
+          s_nch = word_chunks(o);
+          s_phase = uint32_t(o >> 40) & 0xfu;
+          s_run = uint32_t(o >> 44) & 1u;
+          s_level = uint32_t(o >> 45) & 0x3fu;
         }
       }
       s_exit = 0;
       if (got >= 0) {
-        __threadfence();                           // acquire: the phase's inputs
-        const BatchSlotState* b = a.bs + got;
-        s_phase = __ldcg(&b->phase); s_run = __ldcg(&b->run); s_level = __ldcg(&b->level);
-        start = uint32_t(got);
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire: the phase's inputs
       } else if (stopped || *(volatile uint32_t*)&a.bc->finished >= a.n_queries) {
         s_exit = 1;
       } else {
@@ -1780,9 +1824,9 @@ k_batch(const __grid_constant__ BatchArgs a) {
     batch_chunk(a, a.slot[sl], s_phase, s_run, s_level, Part{s_chunk, nch}, buf);
     __syncthreads();
     if (threadIdx.x == 0) {
-      __threadfence();                             // release: this chunk's writes
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");    // release: this chunk's writes
       s_last = atomicAdd(&a.bs[sl].done, 1u) == nch - 1u ? 1u : 0u;
-      if (s_last) __threadfence();                 // acquire: every chunk's writes
+      if (s_last) asm volatile("fence.acq_rel.gpu;" ::: "memory");   // acquire: every chunk's writes
     }
     __syncthreads();
     if (s_last) batch_advance(a, uint32_t(sl));

@@ -165,18 +165,20 @@ def test_large_trace_equals_oracle(large, large_oracle):
 def test_large_mixed_shapes_equal_oracle(large, large_oracle):
     """Batched-mix queries (a head-heavy one reaching hub rows from posting
     lists of 10^5+ nodes, and a tail one): results, E_act and levels through
-    the one-at-a-time and batched paths."""
+    the one-at-a-time, batched and persistent-batch paths."""
     ds, kg, adj, qs = large
     queries, orcs, nhead = large_oracle
     assert nhead >= 2
     batch = kg.search_batch(queries[2:])
-    for q, orc, (bres, bst, status) in zip(queries[2:], orcs[2:], batch):
-        assert status == 0
+    pers = kg.search_batch(queries[2:], persistent=True)
+    for q, orc, (bres, bst, status), (pres, pst, pstatus) in zip(queries[2:], orcs[2:], batch, pers):
+        assert status == 0 and pstatus == 0
         res, st = kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)
         results_match(res, orc)
         results_match(bres, orc)
-        assert st["e_act_central"] == orc.central.e_act == bst["e_act_central"]
-        assert st["levels_central"] == orc.central.last_level
+        results_match(pres, orc)
+        assert st["e_act_central"] == orc.central.e_act == bst["e_act_central"] == pst["e_act_central"]
+        assert st["levels_central"] == orc.central.last_level == pst["levels_central"]
         if orc.marginal is not None:
-            assert st["e_act_marginal"] == orc.marginal.e_act == bst["e_act_marginal"]
-            assert st["levels_marginal"] == orc.marginal.last_level
+            assert st["e_act_marginal"] == orc.marginal.e_act == bst["e_act_marginal"] == pst["e_act_marginal"]
+            assert st["levels_marginal"] == orc.marginal.last_level == pst["levels_marginal"]
