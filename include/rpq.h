@@ -443,7 +443,8 @@ int rpq_server_info(const rpq_server *srv, int32_t *n_slots, int64_t *slot_bytes
 int rpq_server_pages(const rpq_server *srv, int32_t *h_pages, int64_t *h_page_bytes, int32_t *r_pages,
                      int64_t *r_page_bytes, int32_t *peak_running);
 /* Validate and enqueue one query (copied); admits it at once when a slot is
- * free.  Never waits for the device. */
+ * free.  Never waits for the device.  A query whose launch fails completes
+ * with that error (its pages return to the pools) and the call returns it. */
 int rpq_server_submit(rpq_server *srv, const rpq_query *q, uint64_t tag);
 /* Collect finished queries into out (up to max_done), admitting waiting ones
  * into freed slots.  wait != 0 blocks until at least one query has finished
@@ -453,7 +454,8 @@ int rpq_server_poll(rpq_server *srv, rpq_completion *out, int32_t max_done, int3
  * seconds after the call starts (non-decreasing times).  latency_s[i] counts
  * from the scheduled arrival to completion; status[i], n_out[i] and (if out is
  * non-NULL) the results, laid out as in rpq_search_batch, are filled in;
- * *wall_s receives the elapsed time. */
+ * *wall_s receives the elapsed time.  The server must be idle when the call
+ * starts (every query submitted before has been polled), else RPQ_EINVAL. */
 int rpq_server_replay(rpq_server *srv, const rpq_query *qs, const double *arrival_s, int32_t nq,
                       double *latency_s, int32_t *status, int32_t *n_out, rpq_result *out, double *wall_s);
 /* Wait for running queries and release every slot of the server. */

@@ -63,6 +63,8 @@ static double seconds(Clock::time_point a, Clock::time_point b) {
 // reuse them) and central recovery pages.
 static int h_cols(const QueryDev& q) { return std::max(q.n_c, q.n_m); }
 
+static int release_pages(rpq_server* sv, size_t i, bool failed);
+
 // Start waiting queries (in arrival order) while a slot and the head
 // query's pages are free.
 static int admit(rpq_server* sv) {
@@ -99,10 +101,27 @@ static int admit(rpq_server* sv) {
       p.qv.rm[j] = reinterpret_cast<unsigned long long*>(base);
       p.qv.rl[j] = reinterpret_cast<uint32_t*>(base + sizeof(unsigned long long) * sv->slots[i]->d.cap);
     }
-    const int rc = start_query(sv->kg, sv->slots[i], p.qv);
-    if (rc != RPQ_OK) return rc;
-    const cudaError_t e = cudaEventRecord(sv->done_ev[i], sv->slots[i]->st);
-    if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e)); return RPQ_ECUDA; }
+    int rc = start_query(sv->kg, sv->slots[i], p.qv);
+    if (rc == RPQ_OK) {
+      const cudaError_t e = cudaEventRecord(sv->done_ev[i], sv->slots[i]->st);
+      if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e)); rc = RPQ_ECUDA; }
+    }
+    if (rc != RPQ_OK) {
+      // The query could not be started: it completes with its error, and the
+      // slot's pages go back once whatever it launched has finished, so the
+      // queries behind it are not held up.
+      sv->slots[i]->busy = false;
+      rpq_completion c;
+      memset(&c, 0, sizeof(c));
+      c.tag = p.tag;
+      c.status = rc;
+      c.latency_s = seconds(p.t_submit, Clock::now());
+      sv->finished.push_back(c);
+      ++sv->completed;
+      sv->waiting.pop_front();
+      release_pages(sv, i, true);
+      return rc;
+    }
     sv->running[i] = p;
     sv->busy[i] = true;
     sv->waiting.pop_front();
@@ -308,6 +327,14 @@ int rpq_server_replay(rpq_server* sv, const rpq_query* qs, const double* arrival
   }
   for (int32_t i = 1; i < nq; ++i)
     if (arrival_s[i] < arrival_s[i - 1]) { set_error(RPQ_EINVAL, "arrival times must be non-decreasing"); return RPQ_EINVAL; }
+  // completions are matched to the schedule by tag (the query index), so no
+  // query submitted before the call may still be running, waiting or unpolled
+  bool idle = sv->waiting.empty() && sv->finished.empty();
+  for (bool b : sv->busy) idle = idle && !b;
+  if (!idle) {
+    set_error(RPQ_EINVAL, "replay needs an idle server: poll every submitted query first");
+    return RPQ_EINVAL;
+  }
   std::vector<int64_t> base(size_t(nq) + 1, 0);
   for (int32_t i = 0; i < nq; ++i) base[size_t(i) + 1] = base[size_t(i)] + std::max(qs[i].k, 0);
   const Clock::time_point t0 = Clock::now();

@@ -112,6 +112,17 @@ def test_server_rejects_bad_queries(served):
             srv.submit(rpqgen.Query(central=[], marginal=[], k=5, max_depth=4), 1)
         with pytest.raises(rpq.RPQError):
             srv.replay([qs[0], qs[1]], np.array([1.0, 0.5]))      # decreasing arrivals
+        # a replay matches completions to its schedule by query index, so a
+        # query submitted before it must have been polled first
+        srv.submit(qs[0], 77)
+        with pytest.raises(rpq.RPQError):
+            srv.replay([qs[1]], np.zeros(1))
+        got = []
+        while not got:
+            got = srv.poll(wait=True)
+        assert got[0][0] == 77 and got[0][1] == 0 and got[0][2].tobytes() == alone[0].tobytes()
+        res, _, status, _ = srv.replay([qs[1]], np.zeros(1))      # idle again
+        assert status[0] == 0 and res[0].tobytes() == alone[1].tobytes()
     finally:
         srv.close()
 
