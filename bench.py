@@ -57,7 +57,7 @@ FALLBACK_HBM = 6400.0
 # expansion source is unchanged.
 NCU_TRAFFIC = {
     # 8 queries of the large workload, one B300, every k_expand launch (80)
-    "large": {"sha1": "1031d23130ed", "queries": 8, "launches": 80, "dram_bytes": 24152050944},
+    "large": {"sha1": "56b9c58e3ee4", "queries": 8, "launches": 80, "dram_bytes": 24139829248},
 }
 
 

@@ -29,6 +29,7 @@ int dev_err_to_status(uint32_t err) {
   if (err & kErrTimeout) { set_error(RPQ_ETIMEOUT, "a bounded device wait ran out"); return RPQ_ETIMEOUT; }
   if (err & kErrKeyword) { set_error(RPQ_EINVAL, "keyword id out of range (device check)"); return RPQ_EINVAL; }
   if (err & kErrOverflow) { set_error(RPQ_EINTERNAL, "a device work list overflowed"); return RPQ_EINTERNAL; }
+  if (err & kErrBounds) { set_error(RPQ_EINTERNAL, "an index failed its bounds check (checked build)"); return RPQ_EINTERNAL; }
   set_error(RPQ_EINTERNAL, "device consistency check failed (flags 0x%x)", err);
   return RPQ_EINTERNAL;
 }

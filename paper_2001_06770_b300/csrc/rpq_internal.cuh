@@ -50,7 +50,20 @@ enum DevErr : uint32_t {
   kErrOverflow = 1u << 6,  // a work list overflowed its capacity
   kErrInternal = 1u << 7,
   kErrTimeout = 1u << 8,   // a bounded grid barrier ran out
+  kErrBounds = 1u << 9,    // checked build: an index failed its bounds check (the access was skipped)
 };
+
+// Checked build (-DRPQ_CHECKED, librpq_checked.so): the search kernels test
+// the indices they derive from device data (queue and list entries, CSR
+// offsets, neighbour ids, work-list positions) before using them; a failed
+// test sets kErrBounds in *err and the access is skipped, so the query
+// reports RPQ_EINTERNAL and nothing outside a buffer is touched.  In the
+// normal build every test is the constant true and costs nothing.
+#ifdef RPQ_CHECKED
+#define RPQ_IN_BOUNDS(cond, err) ((cond) ? true : (atomicOr((err), ::rpq::kErrBounds), false))
+#else
+#define RPQ_IN_BOUNDS(cond, err) true
+#endif
 
 // Level index of every row, for x = 1..kLvxLevels: for a row with at most
 // kLvxMaxDeg entries, lvx[x-1][v] is the offset (from the row start) of the

@@ -409,7 +409,7 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
       it_len[r] = 0;
       it_seg[r] = 0; it_msk[r] = 0;
       if (uint32_t(r) >= nr) continue;                 // the same in every lane
-      const bool has = cand[r] != kNone;
+      const bool has = cand[r] != kNone && RPQ_IN_BOUNDS(cand[r] < uint32_t(g.n), &c->err);
       if (!__any_sync(0xffffffffu, has)) continue;
       const uint32_t v = has ? cand[r] : 0u;
       if (sparse && has) Fc[v >> 5] = 0;               // every set bit of F_l is in the queue
@@ -470,7 +470,8 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
         uint32_t base = 0;
         if (lane == 0) base = atomicAdd(&c->ncg, uint32_t(__popc(cgb)));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (is_cg) s.cg[base + __popc(cgb & ((1u << lane) - 1u))] = cg_key;
+        const uint32_t at = base + __popc(cgb & ((1u << lane) - 1u));
+        if (is_cg && RPQ_IN_BOUNDS(at < s.cap, &c->err)) s.cg[at] = cg_key;
       }
       bool retain = false;
       if (expand) {
@@ -526,8 +527,10 @@ __device__ __forceinline__ void enqueue_level(const DevKG& g, const DevSlot& s, 
           Item it;
           it.seg_begin = it_seg[r];
           it.off = off;
-          s.items[idx] = it;
-          s.imask[idx] = uint16_t(it_msk[r]);
+          if (RPQ_IN_BOUNDS(idx < s.cap, &c->err)) {
+            s.items[idx] = it;
+            s.imask[idx] = uint16_t(it_msk[r]);
+          }
           t0 = (off + kWarpTile - 1) / kWarpTile;
           t1 = (off + it_len[r] - 1) / kWarpTile;
         }
@@ -648,6 +651,7 @@ __device__ __forceinline__ void target_body(const DevKG& g, const DevSlot& s, Pa
     const uint32_t pr = s.vcl[t / uint32_t(nm)];
     const uint32_t j = t % uint32_t(nm);
     const uint32_t gi = pr >> kNodeBits, v = pr & kNodeMask;
+    if (!RPQ_IN_BOUNDS(v < uint32_t(g.n) && gi < uint32_t(kMaxK), &c->err)) continue;   // same in every lane
     if (c->matched[gi] || ((vis_byte(s.vis, v) >> j) & 1u)) continue;   // same in every lane
     const uint32_t rb = g.row_ptr[v];
     const uint32_t hi = seg_at(g, v, rb, g.row_ptr[v + 1], l + 1);      // entries with a <= l
@@ -657,10 +661,12 @@ __device__ __forceinline__ void target_body(const DevKG& g, const DevSlot& s, Pa
       bool par = false;
       if (e < hi) {
         const uint32_t x = __ldg(g.adj + e);
-        const uint32_t a = x >> kNodeBits, u = x & kNodeMask;
+        const uint32_t a = x >> kNodeBits, u0 = x & kNodeMask;
+        const bool ok = RPQ_IN_BOUNDS(u0 < uint32_t(g.n), &c->err);
+        const uint32_t u = ok ? u0 : 0u;
         const uint32_t vb = vis_byte(s.vis, u), hu = hcol(q, int(j))[u];
         const uint32_t cfw = s.cf[u >> 5], stl = s.stopl[u];
-        if ((vb >> j) & 1u) {
+        if (ok && ((vb >> j) & 1u)) {
           const uint32_t lam = a > hu ? a : hu;
           par = lam == l && !(((cfw >> (u & 31u)) & 1u) && stl <= l);
         }
@@ -865,6 +871,7 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
   uint64_t claims = 0, completed = 0;                // completed: nodes that now hold every central column
   const uint32_t fullc = run == 0 ? (1u << q.n_c) - 1u : 0x100u;
   for (uint32_t t = gw; t < ntiles; t += nwarps) {
+    if (!RPQ_IN_BOUNDS(t < s.tile_cap, &c->err)) break;   // the same in every lane
     const uint32_t t0 = t * kWarpTile;
     const uint32_t t1 = min(t0 + uint32_t(kWarpTile), n_work);
     uint32_t wb = ldx<P>(s.tile_first + t);
@@ -891,13 +898,17 @@ __device__ __forceinline__ bool expand_level(const DevKG& g, const DevSlot& s, i
       const uint32_t seg = __shfl_sync(0xffffffffu, wseg, k);
       const uint32_t msk = __shfl_sync(0xffffffffu, wmsk, k);
       const uint32_t u = u0 + lane;
-      if (u < t1) { e_r[r] = seg + (u - off); m_r[r] = msk; v_r[r] = true; }
+      if (u < t1 && RPQ_IN_BOUNDS(seg + (u - off) < g.m2, &c->err)) { e_r[r] = seg + (u - off); m_r[r] = msk; v_r[r] = true; }
     }
     uint32_t x_r[kExpRounds];
 #pragma unroll
     // the adjacency is streamed (each entry read once per level): evict-first,
     // so that it does not push the visited and frontier lines out of L2
     for (int r = 0; r < kExpRounds; ++r) x_r[r] = v_r[r] ? __ldcs(g.adj + e_r[r]) : 0u;
+#ifdef RPQ_CHECKED
+    for (int r = 0; r < kExpRounds; ++r)
+      if (v_r[r] && !RPQ_IN_BOUNDS((x_r[r] & kNodeMask) < uint32_t(g.n), &c->err)) v_r[r] = false;
+#endif
     uint32_t vb_r[kExpRounds];
 #pragma unroll
     for (int r = 0; r < kExpRounds; ++r) vb_r[r] = v_r[r] ? vis_byte(s.vis, x_r[r] & kNodeMask) : 0xffu;
@@ -1302,13 +1313,15 @@ __device__ void rec_level(const DevKG& g, const DevSlot& s, int j, uint32_t rank
     uint32_t len = 0, rb = 0;
     unsigned long long m = 0;
     if (i < cnt) {
-      const uint32_t qn = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
+      const uint32_t qn0 = i < nseg ? __ldcg(rlist + base + i) : __ldcg(rlist + cap - 1u - (i - nseg));
+      const bool okq = RPQ_IN_BOUNDS(qn0 < uint32_t(g.n), &c->err);
+      const uint32_t qn = okq ? qn0 : 0u;
       // every load of the node first (the addresses depend on qn alone)
       const uint32_t hq = Hj[qn];
       const uint32_t r0 = g.row_ptr[qn], r1 = g.row_ptr[qn + 1];
       const uint32_t o = uint32_t(x) <= kLvxLevels ? g.lvx[size_t(x - 1) * size_t(g.n) + qn] : 0u;
       const unsigned long long mq = __ldcg(rmask + qn);
-      if (i < nseg || hq == uint32_t(x)) {
+      if (okq && (i < nseg || hq == uint32_t(x))) {
         uint32_t hi;                               // first entry with a >= x
         if (uint32_t(x) > kLvxLevels) hi = seg_lower(g.adj, r0, r1, uint32_t(x));
         else if (r1 - r0 <= kLvxMaxDeg) hi = r0 + o;
@@ -1330,8 +1343,10 @@ __device__ void rec_level(const DevKG& g, const DevSlot& s, int j, uint32_t rank
         const uint32_t mid = lo + ((hi - lo + 1) >> 1);
         if (s_off[mid] <= u) lo = mid; else hi = mid - 1;
       }
+      if (!RPQ_IN_BOUNDS(s_rb[lo] + (u - s_off[lo]) < g.m2, &c->err)) continue;
       const uint32_t xe = __ldg(g.adj + s_rb[lo] + (u - s_off[lo]));
       const uint32_t a = xe >> kNodeBits, nb = xe & kNodeMask;
+      if (!RPQ_IN_BOUNDS(nb < uint32_t(g.n), &c->err)) continue;
       // all loads of the neighbour at once, then the tests
       const uint32_t vb = vis_byte(s.vis, nb), hn = Hj[nb], cfw = s.cf[nb >> 5], stl = s.stopl[nb];
       if (!((vb >> j) & 1u)) continue;
@@ -1367,6 +1382,7 @@ __device__ void rec_finish(const DevSlot& s, int j, uint32_t rank, uint32_t R, u
   const uint32_t nov = min(__ldcg(ovf), cap);
   for (uint32_t i = rank * blockDim.x + threadIdx.x; i < nseg + nov; i += stride) {
     const uint32_t v = i < nseg ? __ldcg(rlist + i) : __ldcg(rlist + cap - 1u - (i - nseg));
+    if (!RPQ_IN_BOUNDS(v < uint32_t(s.cap), &c->err)) continue;
     const unsigned long long m = __ldcg(rmask + v);
     rmask[v] = 0;
     if (!holds_central(s, q, v)) continue;

@@ -31,6 +31,15 @@ def test_library_exports_every_declared_symbol():
     assert set(declared_functions()) <= set(rpq.SYMBOLS) | {"rpq_last_error"}
 
 
+def test_checked_library_exports_every_declared_symbol():
+    """The bounds-checked build (device-side index checks compiled in) is the
+    same boundary: it loads on the host and exports every declared call."""
+    from paper_2001_06770_b300 import build as _build
+    L = ctypes.CDLL(_build.build(checked=True))
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
 def test_strerror_names_codes():
     L = rpq.lib()
     assert L.rpq_strerror(0) == b"RPQ_OK"
