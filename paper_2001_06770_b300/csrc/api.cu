@@ -514,6 +514,7 @@ const char* rpq_strerror(int code) {
 const char* rpq_last_error(void) { return g_last_error.c_str(); }
 
 int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
+  ApiRange nvtx_range("rpq_load_kg");
   if (!d || !out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   *out = nullptr;
   if (d->n <= 0 || d->n > RPQ_MAX_NODES) { set_error(RPQ_ELIMIT, "n = %d outside (0, %d]", d->n, RPQ_MAX_NODES); return d->n <= 0 ? RPQ_EINVAL : RPQ_ELIMIT; }
@@ -574,6 +575,7 @@ int rpq_load_kg(const rpq_kg_desc* d, rpq_kg** out) {
 }
 
 int rpq_free_kg(rpq_kg* kg) {
+  ApiRange nvtx_range("rpq_free_kg");
   if (!kg) return RPQ_OK;
   for (Slot* s : kg->slots) destroy_slot(s);
   free_subgraph_scratch(kg);
@@ -598,6 +600,7 @@ int rpq_kg_info(const rpq_kg* kg, int32_t* n, int64_t* m2, int64_t* device_bytes
 }
 
 int rpq_search(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, rpq_stats* stats) {
+  ApiRange nvtx_range("rpq_search");
   if (!kg || !out || !n_out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   QueryDev qv;
   bool empty = false;
@@ -614,6 +617,7 @@ int rpq_search(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, 
 
 int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* out, int32_t* n_out,
                      int32_t* status, rpq_stats* stats) {
+  ApiRange nvtx_range("rpq_search_batch");
   if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
   int nslots = std::max(1, std::min<int>(slot_count(kg), nq));
@@ -655,6 +659,7 @@ int rpq_search_batch(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* ou
 
 int rpq_search_batch_persistent(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq_result* out, int32_t* n_out,
                                 int32_t* status, rpq_stats* stats) {
+  ApiRange nvtx_range("rpq_search_batch_persistent");
   if (!kg || (nq > 0 && (!qs || !out || !n_out || !status))) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (nq < 0) { set_error(RPQ_EINVAL, "nq < 0"); return RPQ_EINVAL; }
   std::vector<int64_t> base(size_t(nq) + 1, 0);
@@ -755,6 +760,7 @@ int rpq_search_batch_persistent(rpq_kg* kg, const rpq_query* qs, int32_t nq, rpq
 }
 
 int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, rpq_stats* stats, rpq_trace_buf* tr) {
+  ApiRange nvtx_range("rpq_trace");
   if (!kg || !out || !n_out || !tr) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   QueryDev qv;
   bool empty = false;
@@ -864,6 +870,7 @@ int rpq_trace(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out, r
 
 int rpq_search_device(rpq_kg* kg, const int32_t* d_keywords, int32_t n_c, int32_t n_m, int32_t k, int32_t max_depth,
                       double gamma, rpq_result* d_out, int32_t* d_n_out) {
+  ApiRange nvtx_range("rpq_search_device");
   if (!kg || !d_keywords || !d_out || !d_n_out) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (n_c < 1 || n_c > kMaxCols || n_m < 0 || n_m > kMaxCols || k < 1 || k > kMaxK || max_depth < 0 ||
       max_depth > kMaxLevel || !(gamma >= 0.0 && gamma <= 1.0)) {
@@ -904,6 +911,7 @@ int rpq_set_tuning(rpq_kg* kg, const rpq_tuning* t) {
 }
 
 int rpq_autotune(rpq_kg* kg, const rpq_query* qs, int32_t nq, int32_t repeats, rpq_tuning* best) {
+  ApiRange nvtx_range("rpq_autotune");
   if (!kg || !qs || nq < 1 || repeats < 1) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
   using Clock = std::chrono::steady_clock;
   std::vector<rpq_result> out(size_t(RPQ_MAX_K) * size_t(nq));
@@ -1022,6 +1030,7 @@ int rpq_transfer_bytes(int32_t k, int64_t* h2d, int64_t* d2h) {
 }
 
 int rpq_sync_device(rpq_kg* kg) {
+  ApiRange nvtx_range("rpq_sync_device");
   if (!kg) { set_error(RPQ_EINVAL, "NULL graph"); return RPQ_EINVAL; }
   if (kg->slots.empty()) return RPQ_OK;
   Slot* s = kg->slots[0];

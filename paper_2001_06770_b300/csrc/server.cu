@@ -208,6 +208,7 @@ static void size_server(const rpq_kg* kg, int64_t budget, int32_t max_slots, int
 }
 
 int rpq_server_create_sized(rpq_kg* kg, int32_t n_slots, int32_t h_pages, int32_t r_pages, rpq_server** out) {
+  ApiRange nvtx_range("rpq_server_create_sized");
   if (!kg || !out || n_slots < 1 || n_slots > 4096 || h_pages < kMaxCols || r_pages < kMaxCols ||
       h_pages > (1 << 20) || r_pages > (1 << 20)) {
     set_error(RPQ_EINVAL, "bad argument (need 1 <= n_slots <= 4096 and %d <= pages <= 2^20)", kMaxCols);
@@ -288,6 +289,7 @@ int rpq_server_pages(const rpq_server* sv, int32_t* h_pages, int64_t* h_page_byt
 }
 
 int rpq_server_submit(rpq_server* sv, const rpq_query* q, uint64_t tag) {
+  ApiRange nvtx_range("rpq_server_submit");
   if (!sv) { set_error(RPQ_EINVAL, "NULL server"); return RPQ_EINVAL; }
   Pending p;
   p.tag = tag;
@@ -303,6 +305,7 @@ int rpq_server_submit(rpq_server* sv, const rpq_query* q, uint64_t tag) {
 }
 
 int rpq_server_poll(rpq_server* sv, rpq_completion* out, int32_t max_done, int32_t* n_done, int32_t wait) {
+  ApiRange nvtx_range("rpq_server_poll");
   if (!sv || !n_done || (max_done > 0 && !out)) { set_error(RPQ_EINVAL, "bad argument"); return RPQ_EINVAL; }
   *n_done = 0;
   int rc = collect(sv, false);
@@ -321,6 +324,7 @@ int rpq_server_poll(rpq_server* sv, rpq_completion* out, int32_t max_done, int32
 
 int rpq_server_replay(rpq_server* sv, const rpq_query* qs, const double* arrival_s, int32_t nq,
                       double* latency_s, int32_t* status, int32_t* n_out, rpq_result* out, double* wall_s) {
+  ApiRange nvtx_range("rpq_server_replay");
   if (!sv || nq < 0 || (nq > 0 && (!qs || !arrival_s || !latency_s || !status || !n_out))) {
     set_error(RPQ_EINVAL, "bad argument");
     return RPQ_EINVAL;
@@ -383,6 +387,7 @@ int rpq_server_replay(rpq_server* sv, const rpq_query* qs, const double* arrival
 }
 
 int rpq_server_destroy(rpq_server* sv) {
+  ApiRange nvtx_range("rpq_server_destroy");
   if (!sv) return RPQ_OK;
   for (size_t i = 0; i < sv->slots.size(); ++i) {
     destroy_slot(sv->slots[i]);

@@ -621,6 +621,7 @@ using namespace rpq;
 
 extern "C" int rpq_search_subgraphs(rpq_kg* kg, const rpq_query* q, rpq_result* out, int32_t* n_out,
                                     rpq_stats* stats, rpq_subgraphs* sgo) {
+  ApiRange nvtx_range("rpq_search_subgraphs");
   if (!kg || !out || !n_out || !sgo) { set_error(RPQ_EINVAL, "NULL argument"); return RPQ_EINVAL; }
   if (sgo->nodes_cap < 0 || sgo->edges_cap < 0 || (sgo->nodes_cap > 0 && !sgo->nodes) ||
       (sgo->edges_cap > 0 && !sgo->edges)) {
