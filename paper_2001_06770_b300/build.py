@@ -41,15 +41,18 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
         return lib
     objdir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
-    for src in sources():
+    objs, jobs = [], []
+    for src in sources():                     # one nvcc per source file, all at once
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = ["nvcc", *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
                "-I", os.path.join(ROOT, "include"), *(["-DRPQ_CHECKED"] if checked else []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
+        jobs.append((cmd, subprocess.Popen(cmd)))
         objs.append(obj)
+    for cmd, job in jobs:
+        if job.wait() != 0:
+            raise subprocess.CalledProcessError(job.returncode, cmd)
     tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
     os.replace(tmp, lib)
