@@ -700,6 +700,8 @@ def run_serve(args, ws, rank, local, wl, ds, qs, kg):
         "server": {k: v for k, v in srv_info.items() if k not in ("running", "waiting")},
         "per_rate": per_rate,
         "latency_ms": {"p50": best["p50_ms"], "p99": best["p99_ms"]},
+        # service latency: the stream at 80% of the measured capacity
+        "latency_ms_below_capacity": {k: v for k, v in per_rate[-1].items() if k != "below_capacity"},
         "one_at_a_time_qps": one_qps,
         "served_vs_one_at_a_time": best["qps"] / one_qps,
         "equal_results_checked": len(sample),
