@@ -39,7 +39,8 @@ extern "C" {
 #define RPQ_ETIMEOUT  (-3)  /* a bounded device wait ran out */
 #define RPQ_ECUDA     (-4)  /* a CUDA runtime call failed */
 #define RPQ_ELIMIT    (-5)  /* input beyond a documented size limit */
-#define RPQ_EINTERNAL (-6)  /* a device-side consistency check failed */
+#define RPQ_EINTERNAL (-6)  /* a device-side consistency check failed (in librpq_checked.so,
+                               also an index that failed its bounds check) */
 #define RPQ_ESIZE     (-7)  /* a caller buffer is too small; the call reports the size needed */
 
 /* Documented limits of the library. */
