@@ -444,8 +444,11 @@ int rpq_server_info(const rpq_server *srv, int32_t *n_slots, int64_t *slot_bytes
 int rpq_server_pages(const rpq_server *srv, int32_t *h_pages, int64_t *h_page_bytes, int32_t *r_pages,
                      int64_t *r_page_bytes, int32_t *peak_running);
 /* Validate and enqueue one query (copied); admits it at once when a slot is
- * free.  Never waits for the device.  A query whose launch fails completes
- * with that error (its pages return to the pools) and the call returns it. */
+ * free.  Never waits for the device.  A query whose start fails completes
+ * with that error as its status (its pages return to the pools, the queries
+ * behind it are admitted as usual).  For tests of that path, the environment
+ * variable RPQ_INJECT_START_FAILURE=k (read when the server is created) makes
+ * the server's k-th query start fail on the host, before any launch. */
 int rpq_server_submit(rpq_server *srv, const rpq_query *q, uint64_t tag);
 /* Collect finished queries into out (up to max_done), admitting waiting ones
  * into freed slots.  wait != 0 blocks until at least one query has finished

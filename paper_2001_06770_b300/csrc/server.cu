@@ -15,6 +15,7 @@
 // same alone or in the mix.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <thread>
@@ -51,6 +52,8 @@ struct rpq_server {
   std::vector<int32_t> h_free, r_free;
   int32_t peak_running = 0;
   int64_t submitted = 0, completed = 0;
+  int64_t starts = 0;                // queries started (or tried)
+  int64_t fail_start_at = 0;         // host-side fault injection: start number k fails (0: never)
 };
 
 namespace rpq {
@@ -101,15 +104,21 @@ static int admit(rpq_server* sv) {
       p.qv.rm[j] = reinterpret_cast<unsigned long long*>(base);
       p.qv.rl[j] = reinterpret_cast<uint32_t*>(base + sizeof(unsigned long long) * sv->slots[i]->d.cap);
     }
-    int rc = start_query(sv->kg, sv->slots[i], p.qv);
+    int rc;
+    if (++sv->starts == sv->fail_start_at) {         // injected on the host, before any launch
+      set_error(RPQ_EINTERNAL, "injected failure of query start %lld", (long long)sv->starts);
+      rc = RPQ_EINTERNAL;
+    } else {
+      rc = start_query(sv->kg, sv->slots[i], p.qv);
+    }
     if (rc == RPQ_OK) {
       const cudaError_t e = cudaEventRecord(sv->done_ev[i], sv->slots[i]->st);
       if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e)); rc = RPQ_ECUDA; }
     }
     if (rc != RPQ_OK) {
-      // The query could not be started: it completes with its error, and the
-      // slot's pages go back once whatever it launched has finished, so the
-      // queries behind it are not held up.
+      // The query could not be started: it completes with its error as its
+      // status, the slot's pages go back once whatever it launched has
+      // finished, and the queries behind it are admitted as usual.
       sv->slots[i]->busy = false;
       rpq_completion c;
       memset(&c, 0, sizeof(c));
@@ -120,7 +129,7 @@ static int admit(rpq_server* sv) {
       ++sv->completed;
       sv->waiting.pop_front();
       release_pages(sv, i, true);
-      return rc;
+      continue;
     }
     sv->running[i] = p;
     sv->busy[i] = true;
@@ -136,20 +145,23 @@ static int admit(rpq_server* sv) {
 // their CG masks at zero (the recovery clears every mask it set); after a
 // failed query they are cleared here.
 static int release_pages(rpq_server* sv, size_t i, bool failed) {
+  int rc = RPQ_OK;
   if (failed) {
     for (int32_t pg : sv->held_r[i]) {
       const cudaError_t e = cudaMemsetAsync(sv->rpool + size_t(pg) * size_t(sv->r_page_bytes), 0,
                                             sizeof(unsigned long long) * sv->slots[i]->d.cap, sv->slots[i]->st);
-      if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)); return RPQ_ECUDA; }
+      if (e != cudaSuccess && rc == RPQ_OK) { set_error(RPQ_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)); rc = RPQ_ECUDA; }
     }
     const cudaError_t e = cudaStreamSynchronize(sv->slots[i]->st);
-    if (e != cudaSuccess) { set_error(RPQ_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e)); return RPQ_ECUDA; }
+    if (e != cudaSuccess && rc == RPQ_OK) { set_error(RPQ_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e)); rc = RPQ_ECUDA; }
   }
+  // the pages go back to the pools in any case (after a failed clear the
+  // device is unusable for the queries that would take them anyway)
   sv->h_free.insert(sv->h_free.end(), sv->held_h[i].begin(), sv->held_h[i].end());
   sv->r_free.insert(sv->r_free.end(), sv->held_r[i].begin(), sv->held_r[i].end());
   sv->held_h[i].clear();
   sv->held_r[i].clear();
-  return RPQ_OK;
+  return rc;
 }
 
 // Collect finished queries; with `block`, wait for at least one if any runs.
@@ -217,6 +229,7 @@ int rpq_server_create_sized(rpq_kg* kg, int32_t n_slots, int32_t h_pages, int32_
   *out = nullptr;
   rpq_server* sv = new rpq_server();
   sv->kg = kg;
+  if (const char* e = getenv("RPQ_INJECT_START_FAILURE")) sv->fail_start_at = atoll(e);
   const size_t cap = size_t(std::max<int32_t>(kg->dev.n, 1));
   sv->h_page_bytes = int64_t((size_t(kg->dev.n) + 15) / 16 * 16);
   sv->r_page_bytes = int64_t((12 * cap + 255) / 256 * 256);

@@ -127,6 +127,50 @@ def test_server_rejects_bad_queries(served):
         srv.close()
 
 
+def test_failed_start_completes_with_its_error():
+    """Host-side fault injection (no GPU fault): the server's third query
+    start fails before any launch.  That query alone completes with an error
+    status, its column pages return to the pools (a server with only the
+    minimum 8 pages of each kind still serves every later query), and every
+    other result equals the query run alone."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = r"""
+import os, sys
+sys.path.insert(0, os.getcwd())
+import rpqgen, paper_2001_06770_b300 as rpq
+from tests.gpu_common import dataset_queries
+ds = rpqgen.make_dataset("small")
+kg = rpq.KG.from_dataset(ds)
+qs = dataset_queries("small", ds, 24, seed=21)
+alone = [kg.search(q.central, q.marginal, q.k, q.max_depth, q.gamma)[0] for q in qs]
+srv = rpq.Server(kg, slots=2, h_pages=8, r_pages=8)
+got = {}
+for i, q in enumerate(qs):
+    srv.submit(q, i)
+    for tag, status, res, st, lat in srv.poll():
+        got[tag] = (status, res)
+while len(got) < len(qs):
+    for tag, status, res, st, lat in srv.poll(wait=True):
+        got[tag] = (status, res)
+    inf = srv.info()      # waiting queries with nothing running would mean lost pages
+    assert inf["running"] > 0 or len(got) == len(qs), ("stuck", inf, len(got))
+failed = [i for i, (status, _) in got.items() if status != 0]
+assert len(failed) == 1 and got[failed[0]][0] == rpq.RPQ_EINTERNAL, failed
+for i, (status, res) in got.items():
+    if status == 0:
+        assert res.tobytes() == alone[i].tobytes(), i
+srv.close()
+kg.close()
+print("injected start failure handled")
+"""
+    env = dict(os.environ, RPQ_INJECT_START_FAILURE="3")
+    r = subprocess.run([sys.executable, "-c", child], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "injected start failure handled" in r.stdout, (r.stdout[-2000:], r.stderr[-2000:])
+
+
 def test_served_mix_equals_oracle():
     """The served workload's shapes (|C| 2-6, |M| 0-8, head and tail keywords,
     k in {5, 10, 20}) on the medium graph, arriving as a Poisson stream faster
